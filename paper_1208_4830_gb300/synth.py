@@ -1,0 +1,134 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module feeds both the CUDA library and the CPU oracle. It draws parameters, epochs, noise
+and batch layouts; it computes no magnification, no quintic and no EA operator, so a mistake in
+either side's arithmetic cannot hide here. Observed fluxes are assembled by the caller as
+F = A_true * (1 + s * z) from the unit-normal draws ``z`` returned here and a magnification
+computed by whichever side is being exercised.
+
+The one geometric step it does take is input shaping: to force a trajectory through a caustic it
+picks a point of the critical curve (the quartic e^{i phi} z^2 (z - d)^2 - (1 + q) z^2 + 2 d z - d^2 = 0,
+i.e. det J = 0) and maps it to the source plane. That is the image-to-source direction of the lens
+map, which the hot path never evaluates (the hot path inverts it).
+
+Parameter rows are theta = (t0, tE, u0, alpha, d, q) (Section 2.1: t_m, t_E, b, theta, a, q);
+fits encode genes (t0, tE, u0, alpha, d, log10 q).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+# gene bounds of the single-lightcurve fit: t0 (Table 1 range of t_m), tE, u0, alpha, d, log10 q
+FIT_LO = np.array([-20.0, 5.0, 0.0, 0.0, 0.3, -4.0])
+FIT_HI = np.array([20.0, 100.0, 1.0, 2.0 * np.pi, 3.0, 0.0])
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def uniform_epochs(n_ep, seed, lo=-60.0, hi=60.0):
+    """n_ep sorted epochs drawn uniformly in [lo, hi] days."""
+    return np.sort(_rng(seed).uniform(lo, hi, n_ep))
+
+
+def prior_theta(n, seed):
+    """Parameter rows from the sweep priors: q log-uniform [1e-4, 1], d log-uniform [0.3, 3],
+    u0 U[0, 1], alpha U[0, 2 pi), tE U[5, 100] d, t0 U[-20, 20] d."""
+    g = _rng(seed)
+    theta = np.empty((n, 6))
+    theta[:, 0] = g.uniform(-20.0, 20.0, n)
+    theta[:, 1] = g.uniform(5.0, 100.0, n)
+    theta[:, 2] = g.uniform(0.0, 1.0, n)
+    theta[:, 3] = g.uniform(0.0, 2.0 * np.pi, n)
+    theta[:, 4] = np.exp(g.uniform(np.log(0.3), np.log(3.0), n))
+    theta[:, 5] = 10.0 ** g.uniform(-4.0, 0.0, n)
+    return theta
+
+
+def _caustic_point(d, q, phi, pick):
+    """A source-plane caustic point of lens (d, q): root number ``pick`` (0..3) of the critical
+    quartic for phase phi, mapped through the image-to-source lens map."""
+    e = np.exp(1j * phi)
+    # e z^2 (z-d)^2 - (1+q) z^2 + 2 d z - d^2, descending powers of z
+    coeffs = [e, -2.0 * d * e, e * d * d - (1.0 + q), 2.0 * d, -d * d]
+    zc = np.roots(coeffs)[pick]
+    zb = np.conj(zc)
+    return zc - 1.0 / zb + q / (d - zb)
+
+
+def force_caustics(theta, frac, seed, t_lo=-50.0, t_hi=50.0):
+    """Re-aim a fraction ``frac`` of the rows so that their trajectory crosses a caustic at a time
+    drawn in [t_lo, t_hi]. The trajectory is zeta(tau) = tau v + u0 w with w = e^{i alpha} and
+    v = -i w, so a crossing point zeta_c fixes u0 = Re(zeta_c conj(w)) and tau_c = Re(zeta_c conj(v));
+    alpha is turned by pi when that u0 is negative. Returns (theta, forced_mask, t_cross), with
+    t_cross NaN for rows left alone."""
+    theta = np.array(theta, dtype=np.float64, copy=True)
+    n = theta.shape[0]
+    g = _rng(seed)
+    forced = np.zeros(n, dtype=bool)
+    idx = g.choice(n, size=int(round(frac * n)), replace=False)
+    forced[idx] = True
+    t_cross = np.full(n, np.nan)
+    for i in np.sort(idx):
+        d, q, tE, alpha = theta[i, 4], theta[i, 5], theta[i, 1], theta[i, 3]
+        zc = _caustic_point(d, q, g.uniform(0.0, 2.0 * np.pi), int(g.integers(0, 4)))
+        w = np.exp(1j * alpha)
+        v = -1j * w
+        u0 = float(np.real(zc * np.conj(w)))
+        tau_c = float(np.real(zc * np.conj(v)))
+        if u0 < 0.0:
+            alpha = (alpha + np.pi) % (2.0 * np.pi)
+            u0, tau_c = -u0, -tau_c
+        t_c = g.uniform(t_lo, t_hi)
+        theta[i, 0] = t_c - tau_c * tE
+        theta[i, 2] = u0
+        theta[i, 3] = alpha
+        t_cross[i] = t_c
+    return theta, forced, t_cross
+
+
+@dataclass
+class Lightcurve:
+    t: np.ndarray          # epochs [d]
+    z: np.ndarray          # unit-normal noise draws, one per epoch
+    sigma_frac: np.ndarray  # per-epoch sigma as a fraction of the true flux
+    truth: np.ndarray      # theta of the injected event
+
+    def observe(self, A_true):
+        """Observed flux and sigma from a magnification of the truth (any implementation)."""
+        sigma = self.sigma_frac * A_true
+        return A_true + sigma * self.z, sigma
+
+
+def single_fit_lightcurve(seed=0):
+    """One lightcurve: truth (t0, tE, u0, alpha, d, q) = (0, 30, 0.1, 1.0, 1.2, 0.01), 400 epochs
+    uniform in [-60, 60] d, Gaussian noise of 1% of the true flux."""
+    g = _rng(seed)
+    t = np.sort(g.uniform(-60.0, 60.0, 400))
+    z = g.standard_normal(400)
+    truth = np.array([0.0, 30.0, 0.1, 1.0, 1.2, 0.01])
+    return Lightcurve(t=t, z=z, sigma_frac=np.full(400, 0.01), truth=truth)
+
+
+@dataclass
+class Sweep:
+    theta: np.ndarray      # (n_cand, 6)
+    forced: np.ndarray     # (n_cand,) trajectories aimed through a caustic
+    t: np.ndarray          # (n_ep,)
+    truth: np.ndarray      # theta whose magnification (plus noise) is the observed flux
+    z: np.ndarray          # (n_ep,) unit-normal noise draws
+    sigma_frac: float
+
+
+def forward_sweep(n_cand=4096, n_ep=2000, seed=0, caustic_frac=0.1):
+    """Candidates from the sweep priors, 10% forced through caustics, epochs uniform in
+    [-60, 60] d; the observed flux is a prior draw plus 1% noise."""
+    theta = prior_theta(n_cand, seed)
+    theta, forced, _ = force_caustics(theta, caustic_frac, seed + 1)
+    t = uniform_epochs(n_ep, seed + 2)
+    truth = prior_theta(1, seed + 3)[0]
+    z = _rng(seed + 4).standard_normal(n_ep)
+    return Sweep(theta=theta, forced=forced, t=t, truth=truth, z=z, sigma_frac=0.01)
