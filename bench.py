@@ -1,0 +1,351 @@
+"""Benchmark of the population-wide fitness evaluation and EA generation on GB300.
+
+One step = one pass of the whole hot path over one batch: a population of 4096 candidates
+(the forward-sweep workload: priors of the sweep, 10% of trajectories aimed through caustics)
+evaluated on a 2000-epoch lightcurve (decode, trajectory, quintic, roots, image selection,
+magnification, chi^2), then ranked, selected, reproduced and mutated into the next population.
+Every step starts from the same population, so the work per step is fixed.
+
+Metric: binary-lens magnifications per second (candidates x epochs per step / step time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores, bounded sample
+
+Under torchrun each rank runs the same workload on its own GPU (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CAND, N_EP = 4096, 2000
+WORKLOAD = "forward sweep: 4096 candidates x 2000 epochs, one EA generation per step"
+# gene domains wide enough for every sweep candidate, including the ones re-aimed at caustics
+BENCH_LO = np.array([-600.0, 5.0, 0.0, 0.0, 0.3, -4.0])
+BENCH_HI = np.array([600.0, 100.0, 3.5, 2.0 * np.pi, 3.0, 0.0])
+METRIC = "binary-lens magnifications/s"
+UNIT = "magnifications/s"
+# FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x maximum SM clock
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# executed FP32 arithmetic per magnification of the forward kernel on this workload, from the
+# ncu instruction counts in profiles/forward_sweep_4096x2000.md (FMA counted as 2 flop)
+FLOP_PER_MAG = {"mixed": None, "fp32": None, "fp64": None}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def sample_clocks_start(device_index):
+    try:
+        f = open(os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv", "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "-i", str(device_index),
+             "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def sample_clocks_stop(handle):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    f.close()
+    rows = []
+    for line in open(f.name):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) == 6 and parts[0].isdigit():
+            rows.append(parts)
+    os.unlink(f.name)
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower().startswith("active")})
+    return {"sm_mhz": statistics.median(int(r[0]) for r in rows), "sm_max_mhz": int(rows[0][1]),
+            "reasons": reasons, "samples": len(rows)}
+
+
+def build_inputs(seed=0):
+    from paper_1208_4830_gb300 import synth
+
+    sw = synth.forward_sweep(N_CAND, N_EP, seed=seed)
+    a = sw.theta.copy()
+    a[:, 5] = np.log10(a[:, 5])
+    P0 = (a - BENCH_LO) / (BENCH_HI - BENCH_LO)
+    assert np.all((P0 >= 0) & (P0 <= 1)), "sweep candidate outside the bench gene domains"
+    return sw, P0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1208_4830_gb300 import sblm, synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sw, P0 = build_inputs()
+    t = torch.tensor(sw.t, device=dev)
+    A_true = sblm.magnification(torch.tensor(sw.truth[None, :], device=dev), t, "fp64")[0]
+    sigma = float(sw.sigma_frac) * A_true
+    flux = A_true + sigma * torch.tensor(sw.z, device=dev)
+    P_in = torch.tensor(P0, device=dev)
+    step_gpu = make_device_step(sblm, P_in, t, flux, sigma, args.precision, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        step_gpu()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fwd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = sample_clocks_start(local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict the inputs from L2 between steps (outside the timed events)
+        ev[k][0].record(stream)
+        step_gpu(fwd_ev[k])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = sample_clocks_stop(clocks)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    fwd_ms = [a.elapsed_time(b) for a, b in fwd_ev]
+    step_ms = float(np.mean(ms))
+    if world > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+
+    # end to end through the C ABI with host buffers: pinned host inputs, host results
+    e2e = run_e2e(sblm, sw, P0, flux.cpu().numpy(), sigma.cpu().numpy(), args) if args.extras else None
+
+    # the other precisions, same step, for context
+    by_prec = {}
+    for prec in (("fp64", "fp32", "mixed") if args.extras else ()):
+        if prec == args.precision:
+            by_prec[prec] = {"ms_per_step": step_ms, "value": N_CAND * N_EP / step_ms * 1e3}
+            continue
+        st = make_device_step(sblm, P_in, t, flux, sigma, prec, dev)
+        st()
+        torch.cuda.synchronize()
+        n = 2 if prec == "fp64" else 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            st()
+        e1.record()
+        torch.cuda.synchronize()
+        m = e0.elapsed_time(e1) / n
+        by_prec[prec] = {"ms_per_step": m, "value": N_CAND * N_EP / m * 1e3}
+
+    if rank == 0:
+        value = world * N_CAND * N_EP / step_ms * 1e3
+        fwd = float(np.mean(fwd_ms))
+        flop = FLOP_PER_MAG.get(args.precision)
+        peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        achieved = flop * N_CAND * N_EP / (fwd * 1e-3) / 1e12 if flop else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "candidates": N_CAND, "epochs": N_EP,
+                       "precision": args.precision, "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"replica x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "kernel": "forward_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel_ms": fwd, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"},
+            "by_precision": by_prec,
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "wall_s": wall,
+        }
+        if args.cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(sw, flux.cpu().numpy(), sigma.cpu().numpy(), args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def make_device_step(sblm, P_in, t, flux, sigma, precision, dev):
+    """One generation through the library: chi^2 of the population from its genes, then the
+    operators into a separate buffer (the input population is reused every step)."""
+    import ctypes
+
+    import torch
+
+    lib = sblm._lib
+    n_pop = P_in.shape[0]
+    p = sblm.params(n_pop=n_pop, n_gen=2, precision=precision, seed=0)
+    P_out = torch.empty_like(P_in)
+    state = sblm.new_state_buffer(dev)
+    sblm.ea_init(torch.empty_like(P_in), 6, p, 0, state)
+    state0 = state.clone()
+    chi = torch.empty(n_pop, dtype=torch.float64, device=dev)
+    theta = torch.empty_like(P_in)
+    lo, hi = torch.tensor(BENCH_LO, device=dev), torch.tensor(BENCH_HI, device=dev)
+
+    def step(fwd_events=None):
+        stream = torch.cuda.current_stream()
+        if fwd_events:
+            fwd_events[0].record(stream)
+        sblm.chi2_genes(P_in, t, flux, sigma, BENCH_LO, BENCH_HI, precision, out=chi)
+        if fwd_events:
+            fwd_events[1].record(stream)
+        P_out.copy_(P_in)
+        state.copy_(state0)
+        sblm.ea_generation(P_out, chi, p, 0, 0, state)
+
+    return step
+
+
+def run_e2e(sblm, sw, P0, flux, sigma, args):
+    """The same step through the public C ABI with host (pinned) buffers: each step copies the
+    population and lightcurve in and the fitness, next population and state out."""
+    import torch
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    P_h, t_h, f_h, s_h = pin(P0), pin(sw.t), pin(flux), pin(sigma)
+    chi_h = torch.empty(N_CAND, dtype=torch.float64).pin_memory()
+    P_out = torch.empty_like(P_h).pin_memory()
+    state = sblm.EAState()
+    p = sblm.params(n_pop=N_CAND, n_gen=2, precision=args.precision, seed=0)
+    init_P = np.empty_like(P0)
+    sblm.ea_init(init_P, 6, p, 0, state)
+    import ctypes
+
+    state0 = sblm.EAState.from_buffer_copy(bytes(state))
+
+    def step():
+        sblm.chi2_genes(P_h, t_h, f_h, s_h, BENCH_LO, BENCH_HI, args.precision, out=chi_h)
+        P_out.copy_(P_h)
+        ctypes.memmove(ctypes.addressof(state), ctypes.addressof(state0), ctypes.sizeof(state))
+        sblm.ea_generation(P_out, chi_h, p, 0, 0, state)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    n = max(3, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    state_bytes = ctypes.sizeof(sblm.EAState)
+    h2d = P0.nbytes + 3 * sw.t.nbytes + P0.nbytes + N_CAND * 8 + state_bytes
+    d2h = N_CAND * 8 + P0.nbytes + state_bytes
+    return {"value": N_CAND * N_EP / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "path": "sblm_chi2_genes + sblm_ea_generation on pinned host buffers"}
+
+
+def cpu_baseline(sw, flux, sigma, seconds):
+    """The FP64 oracle on the host: chi^2 of as many sweep candidates as fit in about
+    `seconds`, one process, one thread."""
+    from oracle import ea as oea
+    from oracle import sblm as osb
+
+    n_done, t_spent = 0, 0.0
+    rows = np.arange(N_CAND)
+    k = 0
+    while t_spent < seconds and k < N_CAND:
+        sel = rows[k : k + 16]
+        t0 = time.perf_counter()
+        osb.chi2(sw.theta[sel], sw.t, flux, sigma)
+        t_spent += time.perf_counter() - t0
+        n_done += sel.size
+        k += 16
+    # the operators of one generation on the full population, amortised per magnification
+    P0 = build_inputs()[1]
+    chi = np.random.default_rng(0).uniform(0, 1e4, N_CAND)
+    op = oea.EAParams(n_pop=N_CAND, seed=0)
+    t0 = time.perf_counter()
+    oea.generation(P0, chi, oea.new_state(op), op, 0)
+    t_ops = time.perf_counter() - t0
+    per_mag = t_spent / (n_done * N_EP) + t_ops / (N_CAND * N_EP)
+    return {"value": 1.0 / per_mag, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_done} of {N_CAND} candidates x {N_EP} epochs (numpy FP64, companion-matrix roots) "
+                      f"+ one generation of operators on all {N_CAND} rows, {t_spent + t_ops:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, on the same workload, a bounded sample per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sw, _ = build_inputs()
+    from oracle import sblm as osb
+
+    A_true = osb.magnification(sw.truth[None, :], sw.t)[0]
+    sigma = sw.sigma_frac * A_true
+    flux = A_true + sigma * sw.z
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(sw, flux, sigma, per_step)
+        if k >= args.warmup:
+            vals.append(cb["value"])
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": N_CAND * N_EP / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "candidates": N_CAND, "epochs": N_EP},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the end-to-end and other-precision measurements (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * sblm.h -- C ABI of the GB300 (sm_103a) library for fitting static binary-lens (SBLM)
+ * point-source microlensing lightcurves with the evolutionary algorithm of
+ * Rajpaul (2012), "Evolutionary algorithm-based analysis of gravitational microlensing
+ * lightcurves".
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Parameter rows theta = (t0, tE, u0, alpha, d, q): t0 = t_m (time of closest approach to the
+ *   primary, days), tE = t_E (Einstein crossing time, days), u0 = b (impact parameter), alpha =
+ *   theta (angle of the impact vector to the +x axis, radians), d = a (lens separation) and q
+ *   (mass ratio), lengths in units of the primary's Einstein angle, primary at the origin,
+ *   secondary on the +x axis (Section 2.1). Rows are stored row-major, 6 doubles each.
+ * - Fit genes are (t0, tE, u0, alpha, d, log10 q), each encoded to [0, 1] by the linear map of
+ *   Eq. (EMMA-encoding) over the bounds [lo_j, hi_j].
+ * - Pointers may address device memory or host memory (pageable or pinned); the library finds
+ *   out which with cudaPointerGetAttributes. Host buffers are copied through an internal
+ *   per-device workspace on `stream`, and a call that touched host memory synchronises `stream`
+ *   before it returns. A call whose buffers are all on the device is asynchronous on `stream`
+ *   unless its description says otherwise.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). All work runs on
+ *   the current CUDA device of the calling thread.
+ * - The caller owns every buffer it passes. The library owns only its workspace, allocated
+ *   lazily per device, grown on demand and kept until process exit; calls that use it are
+ *   serialised by an internal lock.
+ * - Errors are returned, never thrown: arguments are checked on the host before any launch
+ *   (SBLM_EINVAL), CUDA failures map to SBLM_ECUDA, and sblm_last_error() describes the most
+ *   recent failure of the calling thread.
+ */
+#ifndef SBLM_H
+#define SBLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SBLM_OK = 0,
+    SBLM_EINVAL = 1,   /* bad argument: size, pointer, bound, sigma <= 0, non-finite data */
+    SBLM_ENOMEM = 2,   /* workspace allocation failed */
+    SBLM_ECUDA = 3,    /* a CUDA runtime call or launch failed */
+    SBLM_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    SBLM_ENUMERIC = 5  /* non-finite result where a finite one was required */
+} sblm_status;
+
+/* Arithmetic of the forward model. */
+enum {
+    SBLM_FP64 = 0,  /* everything in FP64 */
+    SBLM_MIXED = 1, /* FP32 quintic solve; FP64 re-solve and polish of an epoch when triggered
+                       (|det J| < 1e-3 at an image, two roots closer than 1e-4, or an ambiguous
+                       image classification); chi^2 accumulated in FP64 */
+    SBLM_FP32 = 2   /* FP32 solve, no FP64 re-solve; chi^2 accumulated in FP64 */
+};
+
+#define SBLM_NPAR 6        /* SBLM genes */
+#define SBLM_MAX_NPAR 16   /* largest N_par accepted by the generic EA calls */
+#define SBLM_MAX_WINDOW 15 /* largest stagnation window */
+
+/* Parameter domains [lo_j, hi_j] of Eq. (EMMA-encoding): genes t0, tE, u0, alpha, d, log10 q. */
+typedef struct {
+    double lo[SBLM_NPAR];
+    double hi[SBLM_NPAR];
+} sblm_bounds;
+
+/* Control parameters of the EA (Appendix A); sblm_ea_params_default() fills the paper's. */
+typedef struct {
+    int32_t n_pop;         /* N_pop >= 2 (paper default 1000) */
+    int32_t n_gen;         /* N_gen >= 1 fitness evaluations of the population */
+    double p_mut0;         /* starting jump-mutation probability (paper default 0.01) */
+    int32_t n_tourn;       /* tournament size; 0 -> ceil(N_pop / 25) (paper default) */
+    int32_t stag_window;   /* generations of the stagnation test (10), 1..SBLM_MAX_WINDOW */
+    double stag_rel;       /* stagnant if the best improved by <= stag_rel over the window (0.01) */
+    int32_t restart_after; /* consecutive stagnant generations before a restart (10) */
+    int32_t precision;     /* SBLM_FP64, SBLM_MIXED or SBLM_FP32 for the fitness evaluation */
+    int32_t reserved;      /* must be 0 */
+    uint64_t seed;         /* Philox4x64-10 key word 0; key word 1 is the population's stream id */
+} sblm_ea_params;
+
+/* Dynamic state of one population between generations (Appendix A, "Stagnation checks"). */
+typedef struct {
+    double p_mut;                         /* current jump probability */
+    double best_chi2;                     /* best fitness ever evaluated (archive across restarts) */
+    double hist[SBLM_MAX_WINDOW + 1];     /* best chi^2 of the last stag_window + 1 generations */
+    int32_t n_hist;                       /* entries of hist in use (generations since (re)start) */
+    int32_t stag_run;                     /* consecutive stagnant generations */
+    int32_t n_restarts;                   /* restarts so far */
+    int32_t generation;                   /* generations completed */
+    double best_genes[SBLM_MAX_NPAR];     /* encoded genes of best_chi2 */
+} sblm_ea_state;
+
+/* Human-readable name of a status code (static storage). */
+const char* sblm_status_str(sblm_status s);
+
+/* Description of the calling thread's most recent failure ("" if none). */
+const char* sblm_last_error(void);
+
+/* Fill *p with the paper's defaults: N_pop 1000, N_gen 100, p_mut0 0.01, N_tourn ceil(N_pop/25),
+ * window 10, 1%, restart after 10, SBLM_MIXED, seed 0. */
+void sblm_ea_params_default(sblm_ea_params* p);
+
+/*
+ * Point-source magnification, Section 2.2: for every (candidate c, epoch k), the source position
+ * of Eq. (sourcePos), the five roots of the quintic of Eq. (lensingPoly), rejection of the roots
+ * that do not solve Eq. (lensing), and A = sum_i 1/|det J_i| over the images,
+ * det J = 1 - |1/z^2 + q/(d - z)^2|^2.
+ *   theta  [n_cand * 6]     parameter rows (see conventions), q > 0, d > 0, tE > 0
+ *   t      [n_ep]           epochs in days; ascending order is fastest (roots are carried
+ *                           from one epoch to the next) but not required
+ *   A_out  [n_cand * n_ep]  row-major, written as FP64 whatever the precision
+ *   flags  [n_cand * n_ep]  optional (NULL to skip): bit 0 = classification fell back to the
+ *                           3 (or 5) smallest residuals, bit 1 = an FP64 re-solve ran (MIXED),
+ *                           bit 2 = the root iteration hit its cap, bit 3 = a rejected root was
+ *                           nearly an image (FP32: a close image pair may be unresolved)
+ * n_cand >= 0, n_ep >= 0 (zero sizes return SBLM_OK without a launch). Host theta rows are checked
+ * (finite, tE, d, q > 0); device rows are not, and an invalid row yields NaN or garbage in its
+ * own outputs only.
+ */
+sblm_status sblm_magnification(const double* theta, int32_t n_cand, const double* t, int32_t n_ep,
+                               double* A_out, uint8_t* flags, int32_t precision, void* stream);
+
+/*
+ * chi^2 of every candidate against one lightcurve (Section 4.1):
+ * chi2_out[c] = sum_k ((flux_k - A_ck) / sigma_k)^2, A as in sblm_magnification, the model flux
+ * of a unit, unblended source. The sum runs in FP64 in every precision, in a fixed order, so the
+ * result is deterministic. sigma_k > 0 and finite data are required: host buffers are checked
+ * (SBLM_EINVAL); device buffers are not read back for a check, and bad data there turn into
+ * non-finite chi^2 values (which the EA ranks last). n_ep == 0 gives chi^2 = 0.
+ */
+sblm_status sblm_chi2(const double* theta, int32_t n_cand, const double* t, const double* flux,
+                      const double* sigma, int32_t n_ep, double* chi2_out, int32_t precision,
+                      void* stream);
+
+/*
+ * Fitness of an encoded population (Appendix A, step (a): decode P -> A by Eq. (EMMA-encoding),
+ * then the external fitness function): row i of P [n_pop * 6] holds genes in [0, 1] that decode
+ * to a_j = lo_j + (hi_j - lo_j) p_ij over `bounds`, gene 5 being log10 q; chi2_out[i] is then
+ * computed exactly as sblm_chi2 would for the decoded row. `bounds` is a host struct. The decode
+ * runs inside the forward kernel.
+ */
+sblm_status sblm_chi2_genes(const double* P, int32_t n_pop, const sblm_bounds* bounds, const double* t,
+                            const double* flux, const double* sigma, int32_t n_ep, double* chi2_out,
+                            int32_t precision, void* stream);
+
+/*
+ * Initialisation of a population (Appendix A, "Initialisation"): half the elements of
+ * P [n_pop * n_par] (row-major, encoded genes in [0, 1]) get X ~ U(0,1), the other half the
+ * complement 1 - X of another random element, paired through a Philox-keyed permutation.
+ * `state` (host or device, one sblm_ea_state) is reset: p_mut = p_mut0, empty window, no best.
+ * Random numbers: Philox4x64-10, key (params->seed, stream_id), counter (generation 0, ...).
+ */
+sblm_status sblm_ea_init(double* P, int32_t n_pop, int32_t n_par, const sblm_ea_params* params,
+                         uint64_t stream_id, sblm_ea_state* state, void* stream);
+
+/*
+ * Everything of one generation after the fitness evaluation (Appendix A, steps (b)-(f)):
+ * rank the rows of P by chi2 (stable, NaN last), archive the best ever, tournament selection,
+ * reproduction by Eq. (rep1)/(rep2) with a per-pairing weighting matrix, elitism (row 0 keeps
+ * the fittest row, unmutated), creep then jump mutation of the N_pop - 1 offspring, and the
+ * stagnation check (boost or throttle p_mut; re-initialise after repeated stagnation).
+ *   P     [n_pop * n_par]  in: P(t) as evaluated; out: P(t+1)
+ *   chi2  [n_pop]          fitness of the rows of P(t) (lower is fitter)
+ *   generation             t, the Philox counter word 0 of this generation's draws
+ * Problem-agnostic: any fitness computed by the caller can drive it ("external fitness
+ * function", Appendix A).
+ */
+sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t n_pop, int32_t n_par,
+                               const sblm_ea_params* params, uint64_t stream_id,
+                               int32_t generation, sblm_ea_state* state, void* stream);
+
+/*
+ * Fit the SBLM to one lightcurve (the paper's problem statement: data, parameter domains,
+ * population size, generation budget -> best-fit parameters and their chi^2). Runs the whole
+ * evolutionary sequence of Appendix A on the device: N_gen evaluations of the population with
+ * the forward model of sblm_chi2 in params->precision, the operators of sblm_ea_generation in
+ * between. Synchronous: returns when best_theta (6 doubles: t0, tE, u0, alpha, d, q) and
+ * *best_chi2 are written; they may be host or device pointers. Optional `trace`
+ * [n_gen * 4] doubles (host or device, NULL to skip): per generation the best chi^2 of the
+ * population, p_mut used for its offspring, restarts so far, and the best chi^2 ever.
+ */
+sblm_status sblm_fit(const double* t, const double* flux, const double* sigma, int32_t n_ep,
+                     const sblm_bounds* bounds, const sblm_ea_params* params, double* best_theta,
+                     double* best_chi2, double* trace, void* stream);
+
+/*
+ * Fit n_lc lightcurves of uneven length at once: lightcurve i owns epochs
+ * [offsets[i], offsets[i+1]) of the concatenated t, flux, sigma arrays (offsets [n_lc + 1],
+ * int64, offsets[0] = 0, non-decreasing, each lightcurve at least 1 epoch). Every lightcurve
+ * gets its own population (stream id i) and the full sequence of Appendix A, all inside one
+ * persistent launch. Synchronous; best_theta [n_lc * 6], best_chi2 [n_lc].
+ */
+sblm_status sblm_fit_batch(const double* t, const double* flux, const double* sigma,
+                           const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                           const sblm_ea_params* params, double* best_theta, double* best_chi2,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBLM_H */

@@ -18,8 +18,10 @@ Sequence per generation t (Appendix A, "basic evolutionary sequence"):
 
 Readings where the paper is silent or loose (each listed in the design doc):
 * initialisation pairs element pi(2k) with pi(2k+1) of a random permutation pi of all
-  N_pop*N_par elements (pi = stable argsort of one Philox word per element); the first gets
-  X ~ U(0,1), the second 1 - X; an odd leftover element gets a plain U(0,1);
+  N_pop*N_par elements; pi sorts the elements by a key made of the top 44 bits of one Philox
+  word per element with the element index in the low 20 bits (so no two keys are equal and
+  N_pop*N_par < 2^20); the first of a pair gets X ~ U(0,1), the second 1 - X; an odd leftover
+  element gets a plain U(0,1);
 * ranking is a stable sort on chi^2 with NaN treated as +inf (ties keep row order);
 * the N_tourn tournament draws are with replacement, and a parent may pair with itself;
 * N_pop - 1 offspring come from ceil((N_pop-1)/2) pairings; the last child is dropped when
@@ -62,6 +64,7 @@ OP_MUT = 6
 
 LN_EPS = float(np.log(np.finfo(np.float64).eps))  # ln(2^-52)
 P_MUT_MAX = 0.5
+INIT_INDEX_LIMIT = 1 << 20  # population elements addressable by the initialisation keys
 
 
 @dataclass
@@ -100,9 +103,11 @@ def _draw(params, gen, op, index, sub):
 def init_population(n_pop, n_par, params, gen):
     """Half the elements get X ~ U(0,1); each remaining element gets 1 - X of another random one."""
     m = n_pop * n_par
+    assert m < INIT_INDEX_LIMIT
     e = np.arange(m, dtype=np.uint64)
-    keys = _draw(params, gen, OP_INIT_PERM, e, 0)[:, 0]
-    perm = np.argsort(keys, kind="stable")
+    words = _draw(params, gen, OP_INIT_PERM, e, 0)[:, 0]
+    keys = ((words >> np.uint64(20)) << np.uint64(20)) | e
+    perm = np.argsort(keys)
     n_pairs = m // 2
     x = ph.u01(_draw(params, gen, OP_INIT_U, np.arange(n_pairs + (m % 2), dtype=np.uint64), 0)[:, 0])
     flat = np.empty(m)

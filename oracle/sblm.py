@@ -290,3 +290,25 @@ def paczynski(u):
     """Single point-lens magnification (u^2 + 2) / (u sqrt(u^2 + 4)); used only by pins."""
     u = np.asarray(u, dtype=np.float64)
     return (u * u + 2.0) / (u * np.sqrt(u * u + 4.0))
+
+
+def steepness(theta, t):
+    """Amplification of a relative rounding of the source position into the magnification,
+    |grad_zeta ln A| * max(1, |zeta|), by central differences in the source plane (used to tell
+    points where the magnification is steep, near caustics, from the rest)."""
+    th = np.atleast_2d(np.asarray(theta, dtype=np.float64))
+    zeta = source_position(np.asarray(t, dtype=np.float64)[None, :], th[:, 0:1], th[:, 1:2], th[:, 2:3], th[:, 3:4])
+    d = np.broadcast_to(th[:, 4:5], zeta.shape).ravel()
+    q = np.broadcast_to(th[:, 5:6], zeta.shape).ravel()
+    z = zeta.ravel()
+    h = 1e-6 * np.maximum(1.0, np.abs(z))
+    A = np.empty(z.shape)
+    grad2 = np.zeros(z.shape)
+    for s0 in range(0, z.size, CHUNK):
+        sl = slice(s0, min(z.size, s0 + CHUNK))
+        A[sl] = images(z[sl], d[sl], q[sl])["A"]
+        for step in (h[sl], 1j * h[sl]):
+            ap = images(z[sl] + step, d[sl], q[sl])["A"]
+            am = images(z[sl] - step, d[sl], q[sl])["A"]
+            grad2[sl] += ((ap - am) / (2 * h[sl])) ** 2
+    return (np.sqrt(grad2) / A * np.maximum(1.0, np.abs(z))).reshape(zeta.shape)

@@ -1,0 +1,293 @@
+// ea.cu -- EA operator kernels (Appendix A) and the entry points sblm_ea_init and
+// sblm_ea_generation.
+//
+// One generation after its fitness evaluation takes two launches:
+//   rank_kernel      one block: stable bitonic sort of (chi^2, row) in shared memory, archive of
+//                    the best ever, stagnation check; on a restart it also writes the sort keys
+//                    of the fresh population;
+//   offspring_kernel one thread per reproductive pairing: tournament selection, weighting
+//                    matrix, Eq. (rep1)/(rep2), creep and jump mutation, elitism in row 0; on a
+//                    restart instead one thread per element of the fresh population.
+#include <cmath>
+#include <cstring>
+
+#include "ea_launch.cuh"
+#include "runtime.cuh"
+
+namespace sblm {
+
+namespace {
+
+constexpr int kRankThreads = 1024;
+constexpr int kInitTile = 2048;
+
+__global__ void init_keys_kernel(EAConst c, int gen, uint64_t* __restrict__ keys, int m) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) keys[e] = init_key(c, (uint64_t)gen, (uint64_t)e);
+}
+
+// Element e of the fresh population: its key's rank among all keys (counted against tiles of
+// the key array in shared memory) decides its pairing and value. Every thread of the block
+// takes part in the tile loads.
+__device__ void init_by_rank(const EAConst& c, int gen, const uint64_t* __restrict__ keys, int m,
+                             double* __restrict__ P) {
+    __shared__ uint64_t tile[kInitTile];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t mine = e < m ? keys[e] : 0;
+    uint32_t pos = 0;
+    for (int base = 0; base < m; base += kInitTile) {
+        const int n = min(kInitTile, m - base);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = keys[base + i];
+        __syncthreads();
+        if (e < m)
+            for (int i = 0; i < n; ++i) pos += tile[i] < mine;
+    }
+    if (e < m) P[e] = init_value(c, (uint64_t)gen, pos, (uint64_t)m);
+}
+
+__global__ void init_values_kernel(EAConst c, int gen, const uint64_t* __restrict__ keys, int m,
+                                   double* __restrict__ P) {
+    init_by_rank(c, gen, keys, m, P);
+}
+
+__global__ void state_reset_kernel(EAConst c, sblm_ea_state* state) {
+    if (threadIdx.x != 0) return;
+    sblm_ea_state s;
+    memset(&s, 0, sizeof s);
+    s.p_mut = c.p_mut0;
+    s.best_chi2 = INFINITY;
+    for (int j = 0; j < SBLM_MAX_NPAR; ++j) s.best_genes[j] = NAN;
+    *state = s;
+}
+
+__global__ void __launch_bounds__(kRankThreads)
+    rank_kernel(EAConst c, int gen, const double* __restrict__ chi2, const double* __restrict__ P,
+                sblm_ea_state* __restrict__ state, int* __restrict__ order, EACtrl* __restrict__ ctrl,
+                uint64_t* __restrict__ keys, double* __restrict__ trace_row, int produce) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int n2 = 1;
+    while (n2 < c.n_pop) n2 <<= 1;
+    double* skey = reinterpret_cast<double*>(smem);
+    int* sidx = reinterpret_cast<int*>(skey + n2);
+    __shared__ int s_restart;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        if (i < c.n_pop) {
+            const double v = chi2[i];
+            skey[i] = isnan(v) ? INFINITY : v;
+            sidx[i] = i;
+        } else {
+            skey[i] = INFINITY;
+            sidx[i] = 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    // bitonic sort, ascending in (fitness, row)
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const bool greater = pair_less(skey[l], sidx[l], skey[i], sidx[i]);
+                    if (greater == up) {
+                        const double tk = skey[i];
+                        skey[i] = skey[l];
+                        skey[l] = tk;
+                        const int ti = sidx[i];
+                        sidx[i] = sidx[l];
+                        sidx[l] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < c.n_pop; i += blockDim.x) order[i] = sidx[i];
+    if (threadIdx.x == 0) {
+        sblm_ea_state s = *state;
+        const double best = skey[0];
+        if (best < s.best_chi2) {
+            s.best_chi2 = best;
+            const double* row = P + (size_t)sidx[0] * c.n_par;
+            for (int j = 0; j < c.n_par; ++j) s.best_genes[j] = row[j];
+        }
+        const double p_used = s.p_mut;
+        int restart = 0;
+        if (produce) restart = stagnation_update(s, c, best);
+        s.generation = gen + 1;
+        *state = s;
+        ctrl->p_mut_used = p_used;
+        ctrl->restart = restart;
+        if (trace_row) {
+            trace_row[0] = best;
+            trace_row[1] = p_used;
+            trace_row[2] = (double)s.n_restarts;
+            trace_row[3] = s.best_chi2;
+        }
+        s_restart = restart;
+    }
+    __syncthreads();
+    if (s_restart) {
+        const int m = c.n_pop * c.n_par;
+        for (int e = threadIdx.x; e < m; e += blockDim.x) keys[e] = init_key(c, (uint64_t)(gen + 1), (uint64_t)e);
+    }
+}
+
+__global__ void offspring_kernel(EAConst c, int gen, const double* __restrict__ P, const int* __restrict__ order,
+                                 const EACtrl* __restrict__ ctrl, const uint64_t* __restrict__ keys,
+                                 double* __restrict__ P_next) {
+    if (ctrl->restart) {  // uniform over the grid
+        init_by_rank(c, gen + 1, keys, c.n_pop * c.n_par, P_next);
+        return;
+    }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_par = c.n_par;
+    if (k == 0) {  // elitism: the fittest row survives unmutated
+        const double* e = P + (size_t)order[0] * n_par;
+        for (int j = 0; j < n_par; ++j) P_next[j] = e[j];
+    }
+    const int n_pairs = c.n_pop / 2;  // ceil((N_pop - 1) / 2)
+    if (k >= n_pairs) return;
+    const uint64_t g = (uint64_t)gen;
+    const int ra = tournament(c, g, 2 * (uint64_t)k);
+    const int rb = tournament(c, g, 2 * (uint64_t)k + 1);
+    const double* pa = P + (size_t)order[ra] * n_par;
+    const double* pb = P + (size_t)order[rb] * n_par;
+    const uint32_t mode = uniform_int(philox4x64(g, OP_MODE, (uint64_t)k, 0, c.seed, c.stream).x[0], 3u);
+    const int row1 = 1 + 2 * k, row2 = 2 + 2 * k;
+    const double p_mut = ctrl->p_mut_used;
+    for (int j = 0; j < n_par; ++j) {
+        const uint64_t w = philox4x64(g, OP_F, (uint64_t)k, (uint64_t)j, c.seed, c.stream).x[0];
+        const double f = mode == 0 ? u01(w) : (mode == 1 ? (double)top_bit(w) : 1.0);
+        const double omf = __dsub_rn(1.0, f);
+        const double a = pa[j], b = pb[j];
+        const double c1 = __dadd_rn(__dmul_rn(a, f), __dmul_rn(b, omf));
+        const double c2 = __dadd_rn(__dmul_rn(b, f), __dmul_rn(a, omf));
+        P_next[(size_t)row1 * n_par + j] = mutate_gene(c, g, (uint64_t)row1, (uint64_t)j, c1, p_mut);
+        if (row2 < c.n_pop)
+            P_next[(size_t)row2 * n_par + j] = mutate_gene(c, g, (uint64_t)row2, (uint64_t)j, c2, p_mut);
+    }
+}
+
+int blocks_for(int n, int b) { return (n + b - 1) / b; }
+
+}  // namespace
+
+sblm_status ea_const(const sblm_ea_params* p, int n_pop, int n_par, uint64_t stream_id, EAConst* out) {
+    if (!p) return fail(SBLM_EINVAL, "params is NULL");
+    if (n_pop < 2 || n_pop > kMaxPop) return fail(SBLM_EINVAL, "n_pop=%d outside [2, %d]", n_pop, kMaxPop);
+    if (n_par < 1 || n_par > SBLM_MAX_NPAR) return fail(SBLM_EINVAL, "n_par=%d outside [1, %d]", n_par, SBLM_MAX_NPAR);
+    if ((long)n_pop * n_par >= (1L << kInitIndexBits)) return fail(SBLM_EINVAL, "n_pop * n_par too large");
+    if (p->stag_window < 1 || p->stag_window > SBLM_MAX_WINDOW)
+        return fail(SBLM_EINVAL, "stag_window=%d outside [1, %d]", p->stag_window, SBLM_MAX_WINDOW);
+    if (!(p->p_mut0 >= 0.0 && p->p_mut0 <= 1.0)) return fail(SBLM_EINVAL, "p_mut0 must lie in [0, 1]");
+    if (!(p->stag_rel >= 0.0) || !std::isfinite(p->stag_rel)) return fail(SBLM_EINVAL, "stag_rel must be >= 0");
+    if (p->restart_after < 1) return fail(SBLM_EINVAL, "restart_after must be >= 1");
+    if (p->n_tourn < 0) return fail(SBLM_EINVAL, "n_tourn must be >= 0");
+    if (p->precision < SBLM_FP64 || p->precision > SBLM_FP32) return fail(SBLM_EINVAL, "unknown precision");
+    EAConst c;
+    c.n_pop = n_pop;
+    c.n_par = n_par;
+    c.n_tourn = p->n_tourn > 0 ? p->n_tourn : (n_pop + 24) / 25;
+    c.stag_window = p->stag_window;
+    c.restart_after = p->restart_after;
+    c.p_mut0 = p->p_mut0;
+    c.stag_rel = p->stag_rel;
+    c.seed = p->seed;
+    c.stream = stream_id;
+    *out = c;
+    return SBLM_OK;
+}
+
+cudaError_t launch_init(const EAConst& c, int gen, uint64_t* keys, double* P, cudaStream_t s) {
+    const int m = c.n_pop * c.n_par;
+    init_keys_kernel<<<blocks_for(m, 256), 256, 0, s>>>(c, gen, keys, m);
+    init_values_kernel<<<blocks_for(m, 256), 256, 0, s>>>(c, gen, keys, m, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_reset(const EAConst& c, sblm_ea_state* state, cudaStream_t s) {
+    state_reset_kernel<<<1, 32, 0, s>>>(c, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank(const EAConst& c, int gen, const double* chi2, const double* P, sblm_ea_state* state,
+                        int* order, EACtrl* ctrl, uint64_t* keys, double* trace_row, bool produce, cudaStream_t s) {
+    int n2 = 1;
+    while (n2 < c.n_pop) n2 <<= 1;
+    const size_t smem = (size_t)n2 * (sizeof(double) + sizeof(int));
+    static size_t granted[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (smem > granted[dev & 63]) {  // opt in beyond 48 KB (with the kernel's static shared memory)
+        e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        granted[dev & 63] = smem;
+    }
+    rank_kernel<<<1, kRankThreads, smem, s>>>(c, gen, chi2, P, state, order, ctrl, keys, trace_row, produce ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offspring(const EAConst& c, int gen, const double* P, const int* order, const EACtrl* ctrl,
+                             const uint64_t* keys, double* P_next, cudaStream_t s) {
+    const int m = c.n_pop * c.n_par;
+    offspring_kernel<<<blocks_for(m, 256), 256, 0, s>>>(c, gen, P, order, ctrl, keys, P_next);
+    return cudaGetLastError();
+}
+
+}  // namespace sblm
+
+using namespace sblm;
+
+extern "C" sblm_status sblm_ea_init(double* P, int32_t n_pop, int32_t n_par, const sblm_ea_params* params,
+                                    uint64_t stream_id, sblm_ea_state* state, void* stream) {
+    EAConst c;
+    SBLM_TRY(ea_const(params, n_pop, n_par, stream_id, &c));
+    if (!P || !state) return fail(SBLM_EINVAL, "P and state are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    const int m = n_pop * n_par;
+    int i_P, i_s;
+    SBLM_TRY(st.arg(P, sizeof(double) * m, false, true, &i_P));
+    SBLM_TRY(st.arg(state, sizeof(sblm_ea_state), false, true, &i_s));
+    const int k_keys = st.scratch(sizeof(uint64_t) * m);
+    SBLM_TRY(st.begin());
+    SBLM_CUDA(launch_init(c, 0, static_cast<uint64_t*>(st.scratch_ptr(k_keys)), static_cast<double*>(st.dev(i_P)), s));
+    SBLM_CUDA(launch_state_reset(c, static_cast<sblm_ea_state*>(st.dev(i_s)), s));
+    return st.end();
+}
+
+extern "C" sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t n_pop, int32_t n_par,
+                                          const sblm_ea_params* params, uint64_t stream_id, int32_t generation,
+                                          sblm_ea_state* state, void* stream) {
+    EAConst c;
+    SBLM_TRY(ea_const(params, n_pop, n_par, stream_id, &c));
+    if (!P || !chi2 || !state) return fail(SBLM_EINVAL, "P, chi2 and state are required");
+    if (generation < 0) return fail(SBLM_EINVAL, "generation must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    const int m = n_pop * n_par;
+    int i_P, i_c, i_s;
+    SBLM_TRY(st.arg(P, sizeof(double) * m, true, true, &i_P));
+    SBLM_TRY(st.arg(chi2, sizeof(double) * n_pop, true, false, &i_c));
+    SBLM_TRY(st.arg(state, sizeof(sblm_ea_state), true, true, &i_s));
+    const int k_order = st.scratch(sizeof(int) * n_pop);
+    const int k_ctrl = st.scratch(sizeof(EACtrl));
+    const int k_keys = st.scratch(sizeof(uint64_t) * m);
+    const int k_next = st.scratch(sizeof(double) * m);
+    SBLM_TRY(st.begin());
+    double* dP = static_cast<double*>(st.dev(i_P));
+    double* dN = static_cast<double*>(st.scratch_ptr(k_next));
+    int* order = static_cast<int*>(st.scratch_ptr(k_order));
+    EACtrl* ctrl = static_cast<EACtrl*>(st.scratch_ptr(k_ctrl));
+    uint64_t* keys = static_cast<uint64_t*>(st.scratch_ptr(k_keys));
+    SBLM_CUDA(launch_rank(c, generation, static_cast<const double*>(st.dev(i_c)), dP,
+                          static_cast<sblm_ea_state*>(st.dev(i_s)), order, ctrl, keys, nullptr, true, s));
+    SBLM_CUDA(launch_offspring(c, generation, dP, order, ctrl, keys, dN, s));
+    SBLM_CUDA(cudaMemcpyAsync(dP, dN, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    return st.end();
+}

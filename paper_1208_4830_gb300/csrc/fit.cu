@@ -1,0 +1,127 @@
+// fit.cu -- sblm_fit: the whole evolutionary sequence of Appendix A for one lightcurve on the
+// device. Per generation: the forward model over the population (all SMs), then the ranking
+// block and the offspring kernel; the host only enqueues.
+#include <cmath>
+#include <vector>
+
+#include "ea_launch.cuh"
+#include "forward_launch.cuh"
+#include "runtime.cuh"
+
+namespace sblm {
+
+namespace {
+
+// best genes of the archive -> theta (t0, tE, u0, alpha, d, q) and chi^2
+__global__ void finish_kernel(const sblm_ea_state* __restrict__ state, Bounds b, double* __restrict__ theta,
+                              double* __restrict__ chi2) {
+    if (threadIdx.x != 0) return;
+    double a[SBLM_NPAR];
+    for (int j = 0; j < SBLM_NPAR; ++j) a[j] = b.lo[j] + (b.hi[j] - b.lo[j]) * state->best_genes[j];
+    for (int j = 0; j < 5; ++j) theta[j] = a[j];
+    theta[5] = exp10(a[5]);
+    *chi2 = state->best_chi2;
+}
+
+}  // namespace
+
+sblm_status check_bounds(const sblm_bounds* b, Bounds* out) {
+    if (!b) return fail(SBLM_EINVAL, "bounds is NULL");
+    for (int j = 0; j < SBLM_NPAR; ++j) {
+        if (!std::isfinite(b->lo[j]) || !std::isfinite(b->hi[j]) || !(b->lo[j] < b->hi[j]))
+            return fail(SBLM_EINVAL, "bounds of gene %d must be finite with lo < hi", j);
+        out->lo[j] = b->lo[j];
+        out->hi[j] = b->hi[j];
+    }
+    if (!(b->lo[1] > 0)) return fail(SBLM_EINVAL, "tE bounds must be positive");
+    if (!(b->lo[4] > 0)) return fail(SBLM_EINVAL, "d bounds must be positive");
+    return SBLM_OK;
+}
+
+}  // namespace sblm
+
+using namespace sblm;
+
+extern "C" sblm_status sblm_fit(const double* t, const double* flux, const double* sigma, int32_t n_ep,
+                                const sblm_bounds* bounds, const sblm_ea_params* params, double* best_theta,
+                                double* best_chi2, double* trace, void* stream) {
+    EAConst c;
+    SBLM_TRY(ea_const(params, params ? params->n_pop : 0, SBLM_NPAR, 0, &c));
+    if (params->n_gen < 1) return fail(SBLM_EINVAL, "n_gen must be >= 1");
+    if (n_ep < 1) return fail(SBLM_EINVAL, "n_ep must be >= 1");
+    if (!best_theta || !best_chi2) return fail(SBLM_EINVAL, "best_theta and best_chi2 are required");
+    Bounds b;
+    SBLM_TRY(check_bounds(bounds, &b));
+    const int n_pop = c.n_pop, n_gen = params->n_gen, m = n_pop * SBLM_NPAR;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    int i_t, i_f, i_s, i_th, i_c, i_tr;
+    SBLM_TRY(st.arg(t, sizeof(double) * n_ep, true, false, &i_t));
+    SBLM_TRY(st.arg(flux, sizeof(double) * n_ep, true, false, &i_f));
+    SBLM_TRY(st.arg(sigma, sizeof(double) * n_ep, true, false, &i_s));
+    SBLM_TRY(st.arg(best_theta, sizeof(double) * 6, false, true, &i_th));
+    SBLM_TRY(st.arg(best_chi2, sizeof(double), false, true, &i_c));
+    SBLM_TRY(st.arg(trace, trace ? sizeof(double) * 4 * (size_t)n_gen : 0, false, true, &i_tr));
+    bool d1, d2, d3;
+    SBLM_TRY(is_device_pointer(t, &d1));
+    SBLM_TRY(is_device_pointer(flux, &d2));
+    SBLM_TRY(is_device_pointer(sigma, &d3));
+    if (!d1 && !d2 && !d3) SBLM_TRY(check_lightcurve_host(t, flux, sigma, n_ep));
+    const int k_P0 = st.scratch(sizeof(double) * m);
+    const int k_P1 = st.scratch(sizeof(double) * m);
+    const int k_chi = st.scratch(sizeof(double) * n_pop);
+    const int k_order = st.scratch(sizeof(int) * n_pop);
+    const int k_ctrl = st.scratch(sizeof(EACtrl));
+    const int k_keys = st.scratch(sizeof(uint64_t) * m);
+    const int k_state = st.scratch(sizeof(sblm_ea_state));
+    SBLM_TRY(st.begin());
+
+    double* P[2] = {static_cast<double*>(st.scratch_ptr(k_P0)), static_cast<double*>(st.scratch_ptr(k_P1))};
+    double* chi = static_cast<double*>(st.scratch_ptr(k_chi));
+    int* order = static_cast<int*>(st.scratch_ptr(k_order));
+    EACtrl* ctrl = static_cast<EACtrl*>(st.scratch_ptr(k_ctrl));
+    uint64_t* keys = static_cast<uint64_t*>(st.scratch_ptr(k_keys));
+    sblm_ea_state* state = static_cast<sblm_ea_state*>(st.scratch_ptr(k_state));
+    double* tr = static_cast<double*>(st.dev(i_tr));
+
+    ForwardArgs fa{};
+    fa.from_genes = true;
+    fa.bounds = b;
+    fa.n_cand = n_pop;
+    fa.t = static_cast<const double*>(st.dev(i_t));
+    fa.flux = static_cast<const double*>(st.dev(i_f));
+    fa.sigma = static_cast<const double*>(st.dev(i_s));
+    fa.n_ep = n_ep;
+    fa.chi2_out = chi;
+    fa.mode = params->precision;
+    fa.G = choose_group(n_pop, n_ep);
+
+    SBLM_CUDA(launch_init(c, 0, keys, P[0], s));
+    SBLM_CUDA(launch_state_reset(c, state, s));
+    int cur = 0;
+    for (int g = 0; g < n_gen; ++g) {
+        fa.src = P[cur];
+        SBLM_CUDA(launch_forward(fa, s));
+        const bool produce = g + 1 < n_gen;
+        SBLM_CUDA(launch_rank(c, g, chi, P[cur], state, order, ctrl, keys, tr ? tr + 4 * (size_t)g : nullptr, produce,
+                              s));
+        if (produce) {
+            SBLM_CUDA(launch_offspring(c, g, P[cur], order, ctrl, keys, P[cur ^ 1], s));
+            cur ^= 1;
+        }
+    }
+    finish_kernel<<<1, 32, 0, s>>>(state, b, static_cast<double*>(st.dev(i_th)), static_cast<double*>(st.dev(i_c)));
+    SBLM_TRY(st.end());
+    SBLM_CUDA(cudaStreamSynchronize(s));
+    return SBLM_OK;
+}
+
+extern "C" sblm_status sblm_fit_batch(const double* t, const double* flux, const double* sigma,
+                                      const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                      const sblm_ea_params* params, double* best_theta, double* best_chi2,
+                                      void* stream) {
+    (void)t; (void)flux; (void)sigma; (void)offsets; (void)n_lc; (void)bounds; (void)params;
+    (void)best_theta; (void)best_chi2; (void)stream;
+    return fail(SBLM_EINVAL, "sblm_fit_batch: not available in this build");
+}

@@ -1,0 +1,50 @@
+// forward_launch.cuh -- host interface of the forward-model kernels, shared by the entry points
+// of forward.cu and the fit drivers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/sblm.h"
+
+namespace sblm {
+
+// gene domains of Eq. (EMMA-encoding), passed to kernels by value
+struct Bounds {
+    double lo[SBLM_NPAR];
+    double hi[SBLM_NPAR];
+};
+
+// MIXED: an epoch is re-solved in FP64 when an image has |det J| below this, when two images
+// are closer than the gap trigger, or when the FP32 image selection was ambiguous
+constexpr float kMixedDetTrigger = 1e-3f;
+constexpr float kMixedGapTrigger = 1e-4f;
+
+// largest lightcurve staged in shared memory per block (larger ones are read from global memory)
+constexpr size_t kMaxStagedBytes = 96 * 1024;
+
+struct ForwardArgs {
+    const double* src = nullptr;   // theta rows, or encoded genes when from_genes
+    bool from_genes = false;
+    Bounds bounds{};
+    int n_cand = 0;
+    const double* t = nullptr;
+    const double* flux = nullptr;
+    const double* sigma = nullptr;
+    int n_ep = 0;
+    double* A_out = nullptr;       // optional [n_cand * n_ep]
+    uint8_t* flags = nullptr;      // optional [n_cand * n_ep]
+    double* chi2_out = nullptr;    // optional [n_cand]; null -> no chi^2
+    int mode = SBLM_FP64;
+    int G = 32;                    // threads per candidate (power of two, <= 256)
+};
+
+size_t staged_bytes(int mode, bool chi2, int n_ep);
+int choose_group(int n_cand, int n_ep);
+cudaError_t launch_forward(const ForwardArgs& a, cudaStream_t s);
+sblm_status check_theta_host(const double* theta, int n_cand);
+sblm_status check_lightcurve_host(const double* t, const double* flux, const double* sigma, int n_ep);
+
+}  // namespace sblm

@@ -1,0 +1,286 @@
+"""Python binding of ``libsblm.so`` (the C ABI declared in include/sblm.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA kernels.
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CUDA tensors are passed as device
+pointers on torch's current stream, host arrays as host pointers (the library stages them).
+Importing this module raises if the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsblm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the SBLM kernels have no CPU fallback)"
+    )
+_lib = ctypes.CDLL(LIB_PATH)
+
+FP64, MIXED, FP32 = 0, 1, 2
+NPAR = 6
+MAX_NPAR = 16
+MAX_WINDOW = 15
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
+STATUS = {0: "SBLM_OK", 1: "SBLM_EINVAL", 2: "SBLM_ENOMEM", 3: "SBLM_ECUDA", 4: "SBLM_ETIMEOUT", 5: "SBLM_ENUMERIC"}
+
+
+class Bounds(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * NPAR), ("hi", ctypes.c_double * NPAR)]
+
+
+class EAParams(ctypes.Structure):
+    _fields_ = [
+        ("n_pop", ctypes.c_int32),
+        ("n_gen", ctypes.c_int32),
+        ("p_mut0", ctypes.c_double),
+        ("n_tourn", ctypes.c_int32),
+        ("stag_window", ctypes.c_int32),
+        ("stag_rel", ctypes.c_double),
+        ("restart_after", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class EAState(ctypes.Structure):
+    _fields_ = [
+        ("p_mut", ctypes.c_double),
+        ("best_chi2", ctypes.c_double),
+        ("hist", ctypes.c_double * (MAX_WINDOW + 1)),
+        ("n_hist", ctypes.c_int32),
+        ("stag_run", ctypes.c_int32),
+        ("n_restarts", ctypes.c_int32),
+        ("generation", ctypes.c_int32),
+        ("best_genes", ctypes.c_double * MAX_NPAR),
+    ]
+
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_u64 = ctypes.c_uint64
+_SIGS = {
+    "sblm_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "sblm_last_error": (ctypes.c_char_p, []),
+    "sblm_ea_params_default": (None, [ctypes.POINTER(EAParams)]),
+    "sblm_magnification": (ctypes.c_int, [_p, _i32, _p, _i32, _p, _p, _i32, _p]),
+    "sblm_chi2": (ctypes.c_int, [_p, _i32, _p, _p, _p, _i32, _p, _i32, _p]),
+    "sblm_chi2_genes": (ctypes.c_int, [_p, _i32, ctypes.POINTER(Bounds), _p, _p, _p, _i32, _p, _i32, _p]),
+    "sblm_ea_init": (ctypes.c_int, [_p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _p, _p]),
+    "sblm_ea_generation": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
+    "sblm_fit": (ctypes.c_int, [_p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p, _p]),
+    "sblm_fit_batch": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p],
+    ),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class SBLMError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.sblm_last_error().decode()
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+def _check(status, where):
+    if status != 0:
+        raise SBLMError(status, where)
+
+
+def _precision(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _ptr(x):
+    """(pointer, keep-alive) of a torch tensor or numpy array; None -> NULL."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data, x
+    import torch
+
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr(), x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream, *arrays):
+    """cudaStream_t handle: the given one, else torch's current stream when any array is on the
+    GPU, else the legacy default stream."""
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+
+        if any(isinstance(a, torch.Tensor) and a.is_cuda for a in arrays):
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _like(ref, shape, dtype):
+    """A new output array on the same side (GPU / host) as ``ref``."""
+    try:
+        import torch
+
+        if isinstance(ref, torch.Tensor):
+            tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+            return torch.empty(shape, dtype=tdt, device=ref.device)
+    except ImportError:
+        pass
+    return np.empty(shape, dtype=dtype)
+
+
+def params(**kw):
+    """An EAParams filled with the library's defaults (the paper's), then ``kw``."""
+    p = EAParams()
+    _lib.sblm_ea_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "precision":
+            v = _precision(v)
+        setattr(p, k, v)
+    return p
+
+
+def bounds(lo, hi):
+    b = Bounds()
+    for j in range(NPAR):
+        b.lo[j] = float(lo[j])
+        b.hi[j] = float(hi[j])
+    return b
+
+
+def magnification(theta, t, precision="fp64", flags=False, out=None, flags_out=None, stream=None):
+    """A[c, k] for parameter rows theta [n_cand, 6] at epochs t [n_ep]; optionally per-epoch flags."""
+    n_cand, n_ep = int(theta.shape[0]), int(t.shape[0])
+    if out is None:
+        out = _like(theta, (n_cand, n_ep), np.float64)
+    if flags and flags_out is None:
+        flags_out = _like(theta, (n_cand, n_ep), np.uint8)
+    pt, _a = _ptr(theta)
+    pe, _b = _ptr(t)
+    po, _c = _ptr(out)
+    pf, _d = _ptr(flags_out if flags else None)
+    s = _stream(stream, theta, t, out)
+    _check(_lib.sblm_magnification(pt, n_cand, pe, n_ep, po, pf, _precision(precision), s), "sblm_magnification")
+    return (out, flags_out) if flags else out
+
+
+def chi2(theta, t, flux, sigma, precision="fp64", out=None, stream=None):
+    """chi^2 of each parameter row against the lightcurve (t, flux, sigma)."""
+    n_cand, n_ep = int(theta.shape[0]), int(t.shape[0])
+    if out is None:
+        out = _like(theta, (n_cand,), np.float64)
+    args = [_ptr(a) for a in (theta, t, flux, sigma, out)]
+    s = _stream(stream, theta, t, flux, sigma, out)
+    st = _lib.sblm_chi2(args[0][0], n_cand, args[1][0], args[2][0], args[3][0], n_ep, args[4][0], _precision(precision), s)
+    _check(st, "sblm_chi2")
+    return out
+
+
+def chi2_genes(P, t, flux, sigma, lo, hi, precision="fp64", out=None, stream=None):
+    """chi^2 of each encoded row of P [n_pop, 6] (genes in [0, 1] over the domains [lo, hi],
+    gene 5 = log10 q) against the lightcurve (t, flux, sigma)."""
+    n_pop, n_ep = int(P.shape[0]), int(t.shape[0])
+    if out is None:
+        out = _like(P, (n_pop,), np.float64)
+    b = bounds(lo, hi)
+    args = [_ptr(a) for a in (P, t, flux, sigma, out)]
+    s = _stream(stream, P, t, flux, sigma, out)
+    st = _lib.sblm_chi2_genes(args[0][0], n_pop, ctypes.byref(b), args[1][0], args[2][0], args[3][0], n_ep,
+                              args[4][0], _precision(precision), s)
+    _check(st, "sblm_chi2_genes")
+    return out
+
+
+def new_state_buffer(device=None):
+    """Storage for one sblm_ea_state: a torch uint8 tensor on ``device`` or a host EAState."""
+    if device is None:
+        return EAState()
+    import torch
+
+    return torch.zeros(ctypes.sizeof(EAState), dtype=torch.uint8, device=device)
+
+
+def _state_ptr(state):
+    if isinstance(state, EAState):
+        return ctypes.addressof(state), state
+    return _ptr(state)
+
+
+def read_state(state):
+    """An EAState copy of a state held on the device (or the host struct itself)."""
+    if isinstance(state, EAState):
+        return state
+    raw = state.detach().cpu().numpy().tobytes()
+    return EAState.from_buffer_copy(raw)
+
+
+def ea_init(P, n_par, p, stream_id, state, stream=None):
+    n_pop = int(P.shape[0])
+    pp, _a = _ptr(P)
+    ps, _b = _state_ptr(state)
+    s = _stream(stream, P, state)
+    _check(_lib.sblm_ea_init(pp, n_pop, n_par, ctypes.byref(p), stream_id, ps, s), "sblm_ea_init")
+
+
+def ea_generation(P, chi2_values, p, stream_id, generation, state, stream=None):
+    """In place: P(t) -> P(t+1) given the fitness of the rows of P(t)."""
+    n_pop, n_par = int(P.shape[0]), int(P.shape[1])
+    pp, _a = _ptr(P)
+    pc, _b = _ptr(chi2_values)
+    ps, _c = _state_ptr(state)
+    s = _stream(stream, P, chi2_values, state)
+    st = _lib.sblm_ea_generation(pp, pc, n_pop, n_par, ctypes.byref(p), stream_id, generation, ps, s)
+    _check(st, "sblm_ea_generation")
+
+
+def fit(t, flux, sigma, lo, hi, p, trace=False, stream=None):
+    """Best theta (t0, tE, u0, alpha, d, q) and chi^2 of one lightcurve; optionally the trace."""
+    n_ep = int(t.shape[0])
+    b = bounds(lo, hi)
+    best = np.empty(6)
+    best_chi2 = np.empty(1)
+    tr = np.empty((p.n_gen, 4)) if trace else None
+    a = [_ptr(x) for x in (t, flux, sigma)]
+    ptr_tr, _k = _ptr(tr)
+    s = _stream(stream, t, flux, sigma)
+    st = _lib.sblm_fit(a[0][0], a[1][0], a[2][0], n_ep, ctypes.byref(b), ctypes.byref(p), best.ctypes.data,
+                       best_chi2.ctypes.data, ptr_tr, s)
+    _check(st, "sblm_fit")
+    return (best, float(best_chi2[0]), tr) if trace else (best, float(best_chi2[0]))
+
+
+def fit_batch(t, flux, sigma, offsets, lo, hi, p, stream=None):
+    """Best theta [n_lc, 6] and chi^2 [n_lc] of lightcurves concatenated at ``offsets`` [n_lc + 1]."""
+    n_lc = int(offsets.shape[0]) - 1
+    b = bounds(lo, hi)
+    best = np.empty((n_lc, 6))
+    best_chi2 = np.empty(n_lc)
+    a = [_ptr(x) for x in (t, flux, sigma, offsets)]
+    s = _stream(stream, t, flux, sigma)
+    st = _lib.sblm_fit_batch(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p),
+                             best.ctypes.data, best_chi2.ctypes.data, s)
+    _check(st, "sblm_fit_batch")
+    return best, best_chi2
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares."""
+    return list(_SIGS)

@@ -1,0 +1,109 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry point that
+include/sblm.h declares, and its structs have the layout the binding assumes. Only calls that
+fail argument validation before touching CUDA are made here."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sblm.h")
+LIB = os.path.join(ROOT, "paper_1208_4830_gb300", "libsblm.so")
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not os.path.exists(LIB):
+        from paper_1208_4830_gb300 import build
+
+        build.build()
+    from paper_1208_4830_gb300 import sblm
+
+    return sblm
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sblm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(built):
+    lib = ctypes.CDLL(LIB)
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(built.exported_symbols()) == names
+
+
+def test_struct_layout_matches_header(built, tmp_path):
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "sblm.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(sblm_bounds), sizeof(sblm_ea_params),"
+        " sizeof(sblm_ea_state), offsetof(sblm_ea_params, seed), offsetof(sblm_ea_state, best_genes),"
+        " offsetof(sblm_ea_state, n_hist)); return 0;}\n"
+    )
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    s = built
+    want = [
+        ctypes.sizeof(s.Bounds),
+        ctypes.sizeof(s.EAParams),
+        ctypes.sizeof(s.EAState),
+        s.EAParams.seed.offset,
+        s.EAState.best_genes.offset,
+        s.EAState.n_hist.offset,
+    ]
+    assert got == want
+
+
+def test_status_strings_and_defaults(built):
+    lib = built._lib
+    assert lib.sblm_status_str(0) == b"SBLM_OK"
+    assert lib.sblm_status_str(1) == b"SBLM_EINVAL"
+    p = built.params()
+    # Appendix A defaults: N_pop = 1000, p_mut = 1%, N_tourn = ceil(N_pop/25), 10 generations, 1%
+    assert (p.n_pop, p.p_mut0, p.n_tourn, p.stag_window, p.stag_rel, p.restart_after) == (1000, 0.01, 0, 10, 0.01, 10)
+
+
+def test_argument_validation_without_gpu(built):
+    lib = built._lib
+    # negative sizes and unknown precision are rejected before any CUDA call
+    assert lib.sblm_magnification(None, -1, None, 5, None, None, 0, None) == 1
+    assert b"negative" in lib.sblm_last_error()
+    assert lib.sblm_magnification(None, 3, None, 5, None, None, 9, None) == 1
+    assert lib.sblm_chi2(None, 2, None, None, None, -4, None, 0, None) == 1
+    p = built.params(n_pop=1)
+    assert lib.sblm_ea_generation(None, None, 1, 6, ctypes.byref(p), 0, 0, None, None) == 1
+    p = built.params(n_pop=64, stag_window=99)
+    assert lib.sblm_ea_init(None, 64, 6, ctypes.byref(p), 0, None, None) == 1
+    p = built.params(n_pop=64)
+    assert lib.sblm_ea_init(None, 64, 17, ctypes.byref(p), 0, None, None) == 1
+    b = built.bounds([0, 5, 0, 0, 0.3, -4], [0, 100, 1, 6, 3, 0])  # lo == hi for t0
+    p = built.params(n_pop=64, n_gen=10)
+    assert lib.sblm_fit(None, None, None, 10, ctypes.byref(b), ctypes.byref(p), None, None, None, None) == 1
+    # zero-size work is a successful no-op
+    assert lib.sblm_magnification(None, 0, None, 0, None, None, 0, None) == 0
+
+
+def test_binding_refuses_to_run_without_library(tmp_path):
+    """The binding raises at import when libsblm.so is absent (no CPU fallback)."""
+    import importlib.util
+
+    pkg = tmp_path / "pkg"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_1208_4830_gb300", "sblm.py"), pkg / "sblm.py")
+    spec = importlib.util.spec_from_file_location("sblm_nolib", pkg / "sblm.py")
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError):
+        spec.loader.exec_module(mod)
