@@ -39,8 +39,11 @@ UNIT = "magnifications/s"
 # FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x maximum SM clock
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # executed FP32 arithmetic per magnification of the forward kernel on this workload, from the
-# ncu instruction counts in profiles/forward_sweep_4096x2000.md (FMA counted as 2 flop)
-FLOP_PER_MAG = {"mixed": None, "fp32": None, "fp64": None}
+# ncu thread-level instruction counts (FMA counted as 2 flop), and the kernel's DRAM bytes per
+# launch, from the captures summarised in profiles/forward_kernel_<precision>_sweep_4096x2000.md
+PROFILE = {
+    "mixed": {"flop_per_mag": 3344.0, "traffic": 4.07e6, "file": "profiles/forward_kernel_mixed_sweep_4096x2000.md"},
+}
 
 
 def dist_env():
@@ -173,7 +176,8 @@ def run_gpu(args):
     if rank == 0:
         value = world * N_CAND * N_EP / step_ms * 1e3
         fwd = float(np.mean(fwd_ms))
-        flop = FLOP_PER_MAG.get(args.precision)
+        prof = PROFILE.get(args.precision, {})
+        flop = prof.get("flop_per_mag")
         peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         achieved = flop * N_CAND * N_EP / (fwd * 1e-3) / 1e12 if flop else None
         line = {
@@ -185,8 +189,10 @@ def run_gpu(args):
                        "precision": args.precision, "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replica x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "kernel": "forward_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "kernel_ms": fwd, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"},
+                         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                         "traffic": prof.get("traffic"), "kernel_ms": fwd,
+                         "flop_per_magnification": flop, "profile": prof.get("file"),
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts and clock)"},
             "by_precision": by_prec,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
