@@ -171,6 +171,27 @@ sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t n_pop, int
                                int32_t generation, sblm_ea_state* state, void* stream);
 
 /*
+ * sblm_ea_generation without any allocation. The paper has no counterpart: this is a library
+ * convenience for callers that must not allocate device memory while they run, for example a
+ * pipeline that reserves all of its GPU memory up front and may not grow it later, or a host
+ * thread that cannot afford the device-wide synchronisation that cudaMalloc and cudaFree can
+ * imply. The computation and its results are those of sblm_ea_generation; the differences:
+ * - its scratch lives in one fixed device array compiled into the library (544 KiB plus
+ *   256 bytes, held on every GPU that loads the library until the process exits), so
+ *   n_pop <= 8192 and n_pop * n_par <= 32768; larger sizes return SBLM_EINVAL;
+ * - P, chi2 and state must be device memory (host memory returns SBLM_EINVAL, since staging it
+ *   would need a workspace); the call is asynchronous on `stream` and allocates nothing;
+ * - the first call on a device looks the array's device address up (cudaGetSymbolAddress, with
+ *   that device current); make that first call before any stream capture;
+ * - every call shares the one array, which keeps the last call's contents (nothing in it has to
+ *   start at zero), so calls that overlap on the GPU (other streams, other host threads on the
+ *   same device) race: order them on one stream or synchronise between them.
+ */
+sblm_status sblm_ea_generation_noalloc(double* P, const double* chi2, int32_t n_pop, int32_t n_par,
+                                       const sblm_ea_params* params, uint64_t stream_id,
+                                       int32_t generation, sblm_ea_state* state, void* stream);
+
+/*
  * Fit the SBLM to one lightcurve (the paper's problem statement: data, parameter domains,
  * population size, generation budget -> best-fit parameters and their chi^2). Runs the whole
  * evolutionary sequence of Appendix A on the device: N_gen evaluations of the population with

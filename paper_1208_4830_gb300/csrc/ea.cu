@@ -10,6 +10,7 @@
 //                    restart instead one thread per element of the fresh population.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "ea_launch.cuh"
 #include "runtime.cuh"
@@ -290,4 +291,83 @@ extern "C" sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t
     SBLM_CUDA(launch_offspring(c, generation, dP, order, ctrl, keys, dN, s));
     SBLM_CUDA(cudaMemcpyAsync(dP, dN, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
     return st.end();
+}
+
+// ---------------------------------------------------------------------------------------------
+// sblm_ea_generation_noalloc: the generation above with its scratch (ranking order, control word,
+// initialisation keys, next population) in one fixed device array instead of the workspace.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxPop = 8192;      // largest N_pop
+constexpr int kNoAllocMaxElems = 32768;   // largest N_pop * N_par
+constexpr size_t kNoAllocOrder = 0;                                              // int32 [N_pop]
+constexpr size_t kNoAllocCtrl = kNoAllocOrder + sizeof(int) * kNoAllocMaxPop;    // EACtrl
+constexpr size_t kNoAllocKeys = kNoAllocCtrl + 256;                              // uint64 [M]
+constexpr size_t kNoAllocNext = kNoAllocKeys + sizeof(uint64_t) * kNoAllocMaxElems;  // double [M]
+constexpr size_t kNoAllocBytes = kNoAllocNext + sizeof(double) * kNoAllocMaxElems;   // 544 KiB + 256 B
+
+// Every GPU that loads the library holds this array until the process exits. Its name is a
+// host-side stand-in in host code: kernels get its device address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_ea_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_lock;
+void* g_noalloc_base[64] = {};
+
+// device address of g_ea_scratch on the current device, looked up once per device
+sblm_status noalloc_base(void** out) {
+    int dev = 0;
+    SBLM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SBLM_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_lock);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_ea_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(SBLM_ECUDA, "cudaGetSymbolAddress of the fixed EA scratch failed: %s", cudaGetErrorString(e));
+        }
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return SBLM_OK;
+}
+
+}  // namespace
+
+extern "C" sblm_status sblm_ea_generation_noalloc(double* P, const double* chi2, int32_t n_pop, int32_t n_par,
+                                                  const sblm_ea_params* params, uint64_t stream_id,
+                                                  int32_t generation, sblm_ea_state* state, void* stream) {
+    EAConst c;
+    SBLM_TRY(ea_const(params, n_pop, n_par, stream_id, &c));
+    if (n_pop > kNoAllocMaxPop || (long)n_pop * n_par > kNoAllocMaxElems)
+        return fail(SBLM_EINVAL,
+                    "sblm_ea_generation_noalloc: n_pop=%d, n_par=%d exceed its fixed scratch "
+                    "(n_pop <= %d and n_pop * n_par <= %d)",
+                    n_pop, n_par, kNoAllocMaxPop, kNoAllocMaxElems);
+    if (!P || !chi2 || !state) return fail(SBLM_EINVAL, "P, chi2 and state are required");
+    if (generation < 0) return fail(SBLM_EINVAL, "generation must be >= 0");
+    const void* ptrs[3] = {P, chi2, state};
+    for (const void* p : ptrs) {
+        bool on_dev = false;
+        SBLM_TRY(is_device_pointer(p, &on_dev));
+        if (!on_dev)
+            return fail(SBLM_EINVAL, "sblm_ea_generation_noalloc takes device memory only (%p is host memory)", p);
+    }
+    void* base = nullptr;
+    SBLM_TRY(noalloc_base(&base));
+    char* b = static_cast<char*>(base);
+    int* order = reinterpret_cast<int*>(b + kNoAllocOrder);
+    EACtrl* ctrl = reinterpret_cast<EACtrl*>(b + kNoAllocCtrl);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(b + kNoAllocKeys);
+    double* next = reinterpret_cast<double*>(b + kNoAllocNext);
+    // nothing in the array has to start at zero: the ranking writes order and ctrl (and keys on
+    // a restart) before the offspring kernel reads them, and the offspring kernel writes every
+    // element of next before it is copied into P
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SBLM_CUDA(launch_rank(c, generation, chi2, P, state, order, ctrl, keys, nullptr, true, s));
+    SBLM_CUDA(launch_offspring(c, generation, P, order, ctrl, keys, next, s));
+    SBLM_CUDA(cudaMemcpyAsync(P, next, sizeof(double) * (size_t)n_pop * n_par, cudaMemcpyDeviceToDevice, s));
+    SBLM_CUDA(cudaGetLastError());
+    return SBLM_OK;
 }

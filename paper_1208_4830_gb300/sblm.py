@@ -74,6 +74,7 @@ _SIGS = {
     "sblm_chi2_genes": (ctypes.c_int, [_p, _i32, ctypes.POINTER(Bounds), _p, _p, _p, _i32, _p, _i32, _p]),
     "sblm_ea_init": (ctypes.c_int, [_p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _p, _p]),
     "sblm_ea_generation": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
+    "sblm_ea_generation_noalloc": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_fit": (ctypes.c_int, [_p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p, _p]),
     "sblm_fit_batch": (
         ctypes.c_int,
@@ -249,6 +250,17 @@ def ea_generation(P, chi2_values, p, stream_id, generation, state, stream=None):
     s = _stream(stream, P, chi2_values, state)
     st = _lib.sblm_ea_generation(pp, pc, n_pop, n_par, ctypes.byref(p), stream_id, generation, ps, s)
     _check(st, "sblm_ea_generation")
+
+
+def ea_generation_noalloc(P, chi2_values, p, stream_id, generation, state, stream=None):
+    """As ea_generation, for device tensors only, without any allocation (fixed scratch)."""
+    n_pop, n_par = int(P.shape[0]), int(P.shape[1])
+    pp, _a = _ptr(P)
+    pc, _b = _ptr(chi2_values)
+    ps, _c = _state_ptr(state)
+    s = _stream(stream, P, chi2_values, state)
+    st = _lib.sblm_ea_generation_noalloc(pp, pc, n_pop, n_par, ctypes.byref(p), stream_id, generation, ps, s)
+    _check(st, "sblm_ea_generation_noalloc")
 
 
 def fit(t, flux, sigma, lo, hi, p, trace=False, stream=None):
