@@ -113,7 +113,10 @@ void sblm_ea_params_default(sblm_ea_params* p);
  *   flags  [n_cand * n_ep]  optional (NULL to skip): bit 0 = classification fell back to the
  *                           3 (or 5) smallest residuals, bit 1 = an FP64 re-solve ran (MIXED),
  *                           bit 2 = the root iteration hit its cap, bit 3 = a rejected root was
- *                           nearly an image (FP32: a close image pair may be unresolved)
+ *                           nearly an image (FP32: a close image pair may be unresolved), bit 4 =
+ *                           an image has |det J| < 1e-3, bit 5 = two images closer than 1e-4
+ *                           (bits 4-5: FP32 and MIXED; in MIXED any of bits 0 and 2-5 of the FP32
+ *                           solution triggers the FP64 re-solve, and they stay set beside bit 1)
  * n_cand >= 0, n_ep >= 0 (zero sizes return SBLM_OK without a launch). Host theta rows are checked
  * (finite, tE, d, q > 0); device rows are not, and an invalid row yields NaN or garbage in its
  * own outputs only.
@@ -124,8 +127,10 @@ sblm_status sblm_magnification(const double* theta, int32_t n_cand, const double
 /*
  * chi^2 of every candidate against one lightcurve (Section 4.1):
  * chi2_out[c] = sum_k ((flux_k - A_ck) / sigma_k)^2, A as in sblm_magnification, the model flux
- * of a unit, unblended source. The sum runs in FP64 in every precision, in a fixed order, so the
- * result is deterministic. sigma_k > 0 and finite data are required: host buffers are checked
+ * of a unit, unblended source. The sum runs in FP64-grade arithmetic in every precision (FP32
+ * modes accumulate each thread's epochs as a float pair) and in a fixed order, so FP64 and FP32
+ * results are deterministic; in MIXED the terms of the epochs re-solved in FP64 are added
+ * atomically, so the last bits of a MIXED chi^2 can vary from run to run. sigma_k > 0 and finite data are required: host buffers are checked
  * (SBLM_EINVAL); device buffers are not read back for a check, and bad data there turn into
  * non-finite chi^2 values (which the EA ranks last). n_ep == 0 gives chi^2 = 0.
  */
@@ -216,6 +221,14 @@ sblm_status sblm_fit_batch(const double* t, const double* flux, const double* si
                            const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
                            const sblm_ea_params* params, double* best_theta, double* best_chi2,
                            void* stream);
+
+/*
+ * Measured FMA throughput of the current device, in TFLOP/s (an FMA counts as 2 flop): eight
+ * independent FMA chains per thread over 8 blocks of 256 threads per SM, timed with CUDA events.
+ * Not part of the method: these are the denominators of the ALU roofline that the benchmark
+ * reports for the forward model. Synchronous; uses the workspace.
+ */
+sblm_status sblm_peak_rates(double* fp32_tflops, double* fp64_tflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -75,6 +75,8 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     const int k_ctrl = st.scratch(sizeof(EACtrl));
     const int k_keys = st.scratch(sizeof(uint64_t) * m);
     const int k_state = st.scratch(sizeof(sblm_ea_state));
+    const unsigned qcap = params->precision == SBLM_MIXED ? mixed_queue_capacity(n_pop, n_ep) : 0;
+    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
     SBLM_TRY(st.begin());
 
     double* P[2] = {static_cast<double*>(st.scratch_ptr(k_P0)), static_cast<double*>(st.scratch_ptr(k_P1))};
@@ -96,6 +98,9 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     fa.chi2_out = chi;
     fa.mode = params->precision;
     fa.G = choose_group(n_pop, n_ep);
+    fa.queue = st.scratch_ptr(k_q);
+    fa.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
+    fa.queue_cap = qcap;
 
     SBLM_CUDA(launch_init(c, 0, keys, P[0], s));
     SBLM_CUDA(launch_state_reset(c, state, s));

@@ -36,20 +36,59 @@ __device__ __forceinline__ Cand candidate(const double* __restrict__ src, const 
     return k;
 }
 
-// FP64 re-solve of one deferred epoch (MIXED). Kept out of line: the FP32 state of the calling
-// lane stays on the stack across the call instead of competing with the FP64 solver for registers.
-__device__ __noinline__ double resolve_fp64(const Pending* pq, const Cand* kk, double te, double fe, double we,
-                                            double* A_out, uint8_t* flags, size_t idx, bool chi2) {
+// s + x as an unevaluated pair (hi, lo) of floats: Knuth's two-sum, then renormalisation
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float v = s - hi;
+    const float e = (hi - (s - v)) + (x - v);
+    const float t = lo + e;
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
+// the MIXED re-solve's Aberth stop rule (relative correction), see solve_epoch
+constexpr double kResolveCubic = 1e-6;
+
+// FP64 re-solve of one deferred epoch (MIXED), warm-started from its FP32 roots; returns the
+// chi^2 term. Out of line: an FP32 lane that must do it in place keeps its state on the stack
+// instead of competing with the FP64 solver for registers.
+__device__ __noinline__ double resolve_fp64(const cx<float>* z32, uint32_t why, const Cand* kk, double te,
+                                            double fe, double we, double* A_out, uint8_t* flags, size_t idx,
+                                            bool chi2) {
     cx<double> zz[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) zz[i] = mk<double>(pq->z[i].re, pq->z[i].im);
+    for (int i = 0; i < 5; ++i) zz[i] = mk<double>(z32[i].re, z32[i].im);
     bool w2 = true;
-    const EpochOut<double> o2 = solve_epoch<double>(zeta64(*kk, te), kk->d, kk->q, zz, w2);
+    const EpochOut<double> o2 = solve_epoch<double>(zeta64(*kk, te), kk->d, kk->q, zz, w2, nullptr, kResolveCubic);
     if (A_out) A_out[idx] = o2.A;
-    if (flags) flags[idx] = o2.flag | FLAG_FP64;
+    if (flags) flags[idx] = (uint8_t)(o2.flag | FLAG_FP64 | why);
     if (!chi2) return 0.0;
     const double r = (fe - o2.A) * we;
     return r * r;
+}
+
+// MIXED, second pass: the queued epochs in full warps over the whole GPU. Each chi^2 term is
+// added atomically to its candidate's FP32 partial sum, so the summation order of these terms
+// (and the last bits of a MIXED chi^2) can vary from run to run.
+template <bool CHI2, bool FROM_GENES>
+__global__ void __launch_bounds__(256) resolve_kernel(const double* __restrict__ src, Bounds bounds,
+                                                      const double* __restrict__ t,
+                                                      const double* __restrict__ flux,
+                                                      const double* __restrict__ sigma, int n_ep,
+                                                      const Deferred* __restrict__ queue,
+                                                      const unsigned* __restrict__ count, unsigned cap,
+                                                      double* __restrict__ A_out, uint8_t* __restrict__ flags,
+                                                      double* __restrict__ chi2_out) {
+    const unsigned n = min(*count, cap);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Deferred q = queue[i];
+        const Cand k = candidate<FROM_GENES>(src, bounds, q.c);
+        const double fe = CHI2 ? flux[q.e] : 0.0;
+        const double we = CHI2 ? 1.0 / sigma[q.e] : 0.0;
+        const double term =
+            resolve_fp64(q.z, q.why, &k, t[q.e], fe, we, A_out, flags, (size_t)q.c * n_ep + q.e, CHI2);
+        if (CHI2) atomicAdd(&chi2_out[q.c], term);
+    }
 }
 
 template <int MODE, bool CHI2, bool STAGED, bool FROM_GENES>
@@ -59,7 +98,9 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
                                                          const double* __restrict__ sigma, int n_ep,
                                                          double* __restrict__ A_out,
                                                          uint8_t* __restrict__ flags,
-                                                         double* __restrict__ chi2_out, int G) {
+                                                         double* __restrict__ chi2_out, int G,
+                                                         Deferred* __restrict__ queue,
+                                                         unsigned* __restrict__ queue_count, unsigned queue_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     // staged lightcurve: FP64 mode keeps (t, F, 1/sigma) in FP64; the FP32 modes keep
     // (t_hi, t_lo, F, 1/sigma) as floats, t = t_hi + t_lo split so that t - t0 stays exact
@@ -115,62 +156,17 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
         const float t0h = (float)k.t0, t0l = (float)(k.t0 - (double)t0h);
         const float itE = (float)k.inv_tE, sa = (float)k.sa, ca = (float)k.ca, u0 = (float)k.u0;
         const float d = (float)k.d, q = (float)k.q;
-        const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-        // MIXED: epochs that need FP64 wait in a per-warp queue and are re-solved 32 at a time,
-        // one per lane, instead of stalling the warp behind a single lane
-        Pending* queue = nullptr;
-        Cand* s_cand = nullptr;
-        if constexpr (MODE == SBLM_MIXED) {
-            __shared__ Pending s_queue[kBlock / 32][64];
-            __shared__ Cand s_cands[kBlock];
-            queue = s_queue[warp];
-            s_cand = s_cands;
-            if (G < 32 && g == 0) s_cand[group] = k;
-            __syncwarp();
-        }
-        int qn = 0;  // queue length, equal in every lane of the warp
-        auto resolve = [&](int n) {
-            __syncwarp();
-            double term = 0.0;
-            int grp = -1;
-            if ((int)lane < n) {
-                const Pending* pq = &queue[lane];
-                grp = pq->grp;
-                const Cand* kk = G < 32 ? &s_cand[grp] : &k;
-                const int cc = blockIdx.x * per_block + grp;
-                const int e = pq->e;
-                double te, fe = 0.0, we = 0.0;
-                if (STAGED) {
-                    const float4 ep = s_ep[e];
-                    te = (double)ep.x + (double)ep.y;
-                    fe = ep.z;
-                    we = ep.w;
-                } else {
-                    te = t[e];
-                    if (CHI2) {
-                        fe = flux[e];
-                        we = 1.0 / sigma[e];
-                    }
-                }
-                term = resolve_fp64(pq, kk, te, fe, we, A_out, flags, (size_t)cc * n_ep + e, CHI2);
-            }
-            if (G >= 32) {
-                chi += term;  // every queued epoch belongs to this warp's candidate
-            } else {
-                for (int src_lane = 0; src_lane < n; ++src_lane) {
-                    const double tv = __shfl_sync(0xffffffffu, term, src_lane);
-                    const int gv = __shfl_sync(0xffffffffu, grp, src_lane);
-                    if (gv == group && g == 0) chi += tv;
-                }
-            }
-            __syncwarp();
-        };
+        const unsigned lane = threadIdx.x & 31u;
+        // per-thread chi^2 of the FP32 epochs as an unevaluated float pair (hi + lo): FP64-grade
+        // accumulation on the FP32 pipes; converted to FP64 for the cross-thread reduction
+        float chi_hi = 0.f, chi_lo = 0.f;
         cx<float> z[5];
         bool warm = false;
         for (int it = 0; it < seg; ++it) {
             const int e = e0 + it;
             const bool act = valid && e < e1;
             bool defer = false;
+            uint8_t why = 0;
             if (act) {
                 float4 ep;
                 if (STAGED) {
@@ -183,37 +179,56 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
                 }
                 const float tau = diff_ff(ep.x, ep.y, t0h, t0l) * itE;
                 const cx<float> zeta = mk<float>(tau * sa + u0 * ca, -tau * ca + u0 * sa);
-                const EpochOut<float> o = solve_epoch<float>(zeta, d, q, z, warm);
-                if (MODE == SBLM_MIXED)
-                    defer = (o.flag != 0) || o.min_det < kMixedDetTrigger || o.min_gap < kMixedGapTrigger;
+                EpochOut<float> o = solve_epoch<float>(zeta, d, q, z, warm);
+                o.flag |= (o.min_det < kMixedDetTrigger ? FLAG_NEAR_DET : 0) |
+                          (o.min_gap < kMixedGapTrigger ? FLAG_NEAR_GAP : 0);
+                if (MODE == SBLM_MIXED) defer = o.flag != 0;
+                why = o.flag;
                 if (A_row) A_row[e] = o.A;
                 if (f_row) f_row[e] = o.flag;
                 if (CHI2 && !defer) {
                     const float r = (ep.z - o.A) * ep.w;
-                    chi += (double)(r * r);
+                    ff_add(chi_hi, chi_lo, r * r);
                 }
             }
             if constexpr (MODE == SBLM_MIXED) {
+                // one atomic per warp reserves queue slots for the lanes that defer
                 const unsigned b = __ballot_sync(0xffffffffu, defer);
-                if (defer) {
-                    Pending& pq = queue[qn + __popc(b & ((1u << lane) - 1u))];
+                if (b) {
+                    const int leader = __ffs(b) - 1;
+                    unsigned base = 0;
+                    if ((int)lane == leader) base = atomicAdd(queue_count, (unsigned)__popc(b));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (defer) {
+                        const unsigned slot = base + __popc(b & ((1u << lane) - 1u));
+                        if (slot < queue_cap) {
+                            Deferred& q = queue[slot];
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) pq.z[i] = z[i];
-                    pq.e = e;
-                    pq.grp = group;
-                }
-                qn += __popc(b);
-                if (qn >= 32) {
-                    resolve(32);
-                    if ((int)lane < qn - 32) queue[lane] = queue[32 + lane];
-                    qn -= 32;
-                    __syncwarp();
+                            for (int i = 0; i < 5; ++i) q.z[i] = z[i];
+                            q.c = c;
+                            q.e = e;
+                            q.why = why;
+                        } else {  // queue full: re-solve here
+                            double te, fe = 0.0, we = 0.0;
+                            if (STAGED) {
+                                const float4 ep = s_ep[e];
+                                te = (double)ep.x + (double)ep.y;
+                                fe = ep.z;
+                                we = ep.w;
+                            } else {
+                                te = t[e];
+                                if (CHI2) {
+                                    fe = flux[e];
+                                    we = 1.0 / sigma[e];
+                                }
+                            }
+                            chi += resolve_fp64(z, why, &k, te, fe, we, A_out, flags, (size_t)c * n_ep + e, CHI2);
+                        }
+                    }
                 }
             }
         }
-        if constexpr (MODE == SBLM_MIXED) {
-            if (qn > 0) resolve(qn);
-        }
+        chi += (double)chi_hi + (double)chi_lo;
     }
     if (!CHI2) return;
     // deterministic reduction over the candidate's G threads
@@ -252,7 +267,13 @@ cudaError_t launch_t(const ForwardArgs& a, cudaStream_t s) {
     const int per_block = kBlock / a.G;
     const int grid = (a.n_cand + per_block - 1) / per_block;
     kern<<<grid, kBlock, smem, s>>>(a.src, a.bounds, a.n_cand, a.t, a.flux, a.sigma, a.n_ep, a.A_out, a.flags,
-                                    a.chi2_out, a.G);
+                                    a.chi2_out, a.G, static_cast<Deferred*>(a.queue), a.queue_count, a.queue_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || MODE != SBLM_MIXED || a.queue_cap == 0) return e;
+    const int rgrid = (int)std::min<unsigned>((a.queue_cap + 255) / 256, 152u * 8u);
+    resolve_kernel<CHI2, FROM_GENES><<<rgrid, 256, 0, s>>>(a.src, a.bounds, a.t, a.flux, a.sigma, a.n_ep,
+                                                          static_cast<const Deferred*>(a.queue), a.queue_count,
+                                                          a.queue_cap, a.A_out, a.flags, a.chi2_out);
     return cudaGetLastError();
 }
 
@@ -281,8 +302,19 @@ int choose_group(int n_cand, int n_ep) {
     return (int)std::max(1L, std::min(g, cap));
 }
 
+unsigned mixed_queue_capacity(int n_cand, int n_ep) {
+    const long n = (long)n_cand * n_ep / 32;
+    return (unsigned)std::min<long>(std::max<long>(n, 4096), 1L << 24);
+}
+
+size_t deferred_entry_bytes() { return sizeof(Deferred); }
+
 cudaError_t launch_forward(const ForwardArgs& a, cudaStream_t s) {
     if (a.n_cand <= 0 || a.n_ep <= 0) return cudaSuccess;
+    if (a.mode == SBLM_MIXED && a.queue_cap > 0) {
+        cudaError_t e = cudaMemsetAsync(a.queue_count, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
     const bool chi2 = a.chi2_out != nullptr;
     switch (a.mode) {
         case SBLM_FP64: return chi2 ? launch_m<SBLM_FP64, true>(a, s) : launch_m<SBLM_FP64, false>(a, s);
@@ -329,6 +361,8 @@ extern "C" sblm_status sblm_magnification(const double* theta, int32_t n_cand, c
     SBLM_TRY(st.arg(t, sizeof(double) * (size_t)n_ep, true, false, &i_t));
     SBLM_TRY(st.arg(A_out, sizeof(double) * (size_t)n_cand * n_ep, false, true, &i_A));
     SBLM_TRY(st.arg(flags, flags ? (size_t)n_cand * n_ep : 0, false, true, &i_f));
+    const unsigned qcap = precision == SBLM_MIXED ? mixed_queue_capacity(n_cand, n_ep) : 0;
+    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
     bool on_dev = true;
     SBLM_TRY(is_device_pointer(theta, &on_dev));
     if (!on_dev) SBLM_TRY(check_theta_host(theta, n_cand));
@@ -344,6 +378,9 @@ extern "C" sblm_status sblm_magnification(const double* theta, int32_t n_cand, c
     a.flags = static_cast<uint8_t*>(st.dev(i_f));
     a.mode = precision;
     a.G = choose_group(n_cand, n_ep);
+    a.queue = st.scratch_ptr(k_q);
+    a.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
+    a.queue_cap = qcap;
     SBLM_CUDA(launch_forward(a, s));
     return st.end();
 }
@@ -368,6 +405,8 @@ static sblm_status chi2_impl(const double* src, bool genes, const Bounds& b, int
     SBLM_TRY(st.arg(flux, sizeof(double) * (size_t)n_ep, true, false, &i_f));
     SBLM_TRY(st.arg(sigma, sizeof(double) * (size_t)n_ep, true, false, &i_s));
     SBLM_TRY(st.arg(chi2_out, sizeof(double) * (size_t)n_cand, false, true, &i_c));
+    const unsigned qcap = precision == SBLM_MIXED ? mixed_queue_capacity(n_cand, n_ep) : 0;
+    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
     bool on_dev = true;
     SBLM_TRY(is_device_pointer(src, &on_dev));
     if (!on_dev && !genes) SBLM_TRY(check_theta_host(src, n_cand));
@@ -395,6 +434,9 @@ static sblm_status chi2_impl(const double* src, bool genes, const Bounds& b, int
     a.chi2_out = static_cast<double*>(st.dev(i_c));
     a.mode = precision;
     a.G = choose_group(n_cand, n_ep);
+    a.queue = st.scratch_ptr(k_q);
+    a.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
+    a.queue_cap = qcap;
     SBLM_CUDA(launch_forward(a, s));
     return st.end();
 }

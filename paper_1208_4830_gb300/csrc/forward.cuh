@@ -17,17 +17,21 @@ namespace sblm {
 // a root whose residual lies between `lens` and this is neither clearly an image nor clearly
 // spurious (an image pair the arithmetic could not resolve drops out with opposite parities,
 // leaving the count and parity tests satisfied), so the epoch is flagged. `polish`: most Newton
-// steps per root (fewer once a step is below the rounding level).
+// steps per root (fewer once a step is below the rounding level). `cubic`: a root whose Aberth
+// correction is below this (relative) is done: the iteration converges cubically, so after that
+// update its error is far below the lens-equation polish's reach.
 template <typename T>
 struct Tol;
 template <>
 struct Tol<double> {
-    static constexpr double step = 1e-13, lens = 1e-10, pair = 1e-8, dup = 1e-9, shift = 1e-12, ambiguous = 0.0;
+    static constexpr double step = 1e-13, lens = 1e-10, pair = 1e-8, dup = 1e-9, shift = 1e-12, ambiguous = 0.0,
+                            cubic = 1e-13;
     static constexpr int cap_cold = 120, cap_warm = 40, polish = 2;
 };
 template <>
 struct Tol<float> {
-    static constexpr float step = 2e-6f, lens = 2e-6f, pair = 2e-5f, dup = 1e-5f, shift = 1e-6f, ambiguous = 1e-2f;
+    static constexpr float step = 2e-6f, lens = 2e-6f, pair = 2e-5f, dup = 1e-5f, shift = 1e-6f, ambiguous = 1e-2f,
+                           cubic = 1e-3f;
     static constexpr int cap_cold = 100, cap_warm = 30, polish = 4;
 };
 
@@ -45,7 +49,14 @@ struct Eps<float> {
 constexpr float kNoise = 16.0f;
 
 // flags written per (candidate, epoch)
-enum : uint8_t { FLAG_FALLBACK = 1, FLAG_FP64 = 2, FLAG_CAP = 4, FLAG_AMBIGUOUS = 8 };
+enum : uint8_t {
+    FLAG_FALLBACK = 1,     // image selection fell back to the residual ranking
+    FLAG_FP64 = 2,         // MIXED: the epoch was re-solved in FP64
+    FLAG_CAP = 4,          // the root iteration hit its cap
+    FLAG_AMBIGUOUS = 8,    // a root's residual lay in the band between image and spurious
+    FLAG_NEAR_DET = 16,    // an image has |det J| below the MIXED trigger (next to a caustic)
+    FLAG_NEAR_GAP = 32     // two images are closer than the MIXED trigger
+};
 
 // ------------------------------------------------------------------------------------------
 // Eq. (lensingPoly), for a lens of mass m1 at the origin and m2 at z = a:
@@ -121,11 +132,12 @@ __device__ __forceinline__ void cold_start(const cx<T> c[6], cx<T> z[5]) {
 // Aberth-Ehrlich simultaneous iteration, Gauss-Seidel sweep (each root uses the newest values
 // of the others). A root stops moving once |p(z)| is at the rounding level of its Horner
 // evaluation, kNoise * eps * sum_k |c_k| |z|^k (nothing finer can be resolved in T), or once its
-// correction is below Tol::step relative. Only the roots in the bit mask `active` move; the
+// correction is below Tol::cubic relative. Only the roots in the bit mask `active` move; the
 // others still repel them. Returns the number of sweeps, or -1 if `cap` sweeps did not converge.
 template <typename T>
-__device__ __forceinline__ int aberth(const cx<T> c[6], cx<T> z[5], int cap, unsigned active = 31u) {
-    const T tol2 = Tol<T>::step * Tol<T>::step;
+__device__ __forceinline__ int aberth(const cx<T> c[6], cx<T> z[5], int cap, unsigned active = 31u,
+                                     T cubic = Tol<T>::cubic) {
+    const T tol2 = cubic * cubic;
     T ac[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) ac[k] = sqrt_(norm2(c[k]));
@@ -170,14 +182,17 @@ struct EpochOut {
     T A;         // sum of 1/|det J| over the images
     T min_det;   // smallest |det J| over the images
     T min_gap;   // smallest distance between two images
+    int sweeps;  // root-iteration sweeps spent (diagnostics)
     uint8_t flag;
 };
 
-// a root set carried between epochs, and the epoch it belongs to, for a deferred re-solve
-struct Pending {
+// an epoch that MIXED re-solves in FP64: its FP32 roots (the warm start), candidate, epoch and
+// the flags that triggered it
+struct Deferred {
     cx<float> z[5];
+    int c;
     int e;
-    int grp;
+    uint32_t why;
 };
 
 // A root of the quintic, kept either as z (origin at the primary) or, next to the secondary, as
@@ -203,6 +218,9 @@ __device__ __forceinline__ void lens_terms(const Root<T>& r, cx<T> zeta, T d, T 
     K = ib * ib + q * (idz * idz);
     qterm = q * sqrt_(norm2(idz));
 }
+
+// roots whose relative lens-equation residual exceeds this are spurious without a polish
+constexpr float kSpurious = 0.05f;
 
 // Spurious-root rejection (Section 2.2: substitution into Eq. (lensing)) and magnification.
 // Each root gets `polish` Newton steps on the lens equation itself,
@@ -238,25 +256,25 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
         for (int s = 0; s <= Tol<T>::polish; ++s) {
             lens_terms(r, zeta, d, q, f, K, qt);
             if (s == Tol<T>::polish) break;
-            const T dj = T(1) - norm2(K);
-            bool moved_enough = false;
-            if (fabs(dj) >= T(1e-30)) {
-                const cx<T> num = (K * conj(f)) - f;
-                const cx<T> delta = rcp(fabs(dj)) * (dj < T(0) ? -num : num);
-                if (finite2(delta)) {
-                    const T ref2 = r.local ? norm2(r.w) : norm2(r.z);
-                    moved_enough = norm2(delta) > T(4) * Eps<T>::value * Eps<T>::value * ref2;
-                    if (r.local) {
-                        r.w = r.w + delta;
-                        r.z = mk<T>(d, T(0)) + r.w;
-                    } else {
-                        r.z = r.z + delta;
-                    }
-                }
+            if (s == 0) {
+                // a root whose residual is far beyond the ambiguous band is spurious: no polish
+                const T az2 = norm2(r.z);
+                const T sc = sqrt_(az2) + rsqrt_(az2) + qt + zeta_abs;
+                if (norm2(f) > T(kSpurious) * T(kSpurious) * sc * sc) break;
             }
-            if (!moved_enough) {  // converged: the last step changed nothing resolvable
-                lens_terms(r, zeta, d, q, f, K, qt);
-                break;
+            const T dj = T(1) - norm2(K);
+            if (!(fabs(dj) >= T(1e-30))) break;
+            const cx<T> num = (K * conj(f)) - f;
+            const cx<T> delta = rcp(fabs(dj)) * (dj < T(0) ? -num : num);
+            if (!finite2(delta)) break;
+            const T ref2 = r.local ? norm2(r.w) : norm2(r.z);
+            // converged: this step is below the rounding level, keep (f, K) of this position
+            if (norm2(delta) <= T(4) * Eps<T>::value * Eps<T>::value * ref2) break;
+            if (r.local) {
+                r.w = r.w + delta;
+                r.z = mk<T>(d, T(0)) + r.w;
+            } else {
+                r.z = r.z + delta;
             }
         }
         const cx<T> moved = r.local ? r.w - rr[i].w : r.z - rr[i].z;
@@ -350,19 +368,21 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
     return out;
 }
 
-// Roots closer to the secondary than kLocalFrac * d are refined on the quintic written in the
-// secondary's frame (masses (q, 1) at (0, -d), source zeta - d), whose low-order coefficients
-// carry q with full relative precision: in the primary's frame a pair of roots a few q apart
-// next to the secondary is not resolved in FP32.
+// When two or more roots lie closer to the secondary than kLocalFrac * d, they are refined on the
+// quintic written in the secondary's frame (masses (q, 1) at (0, -d), source zeta - d), whose
+// low-order coefficients carry q with full relative precision: in the primary's frame a cluster
+// of roots next to the secondary (a few q apart for a small q) is not resolved in FP32.
 constexpr float kLocalFrac = 0.1f;
 
 // One epoch in arithmetic T: quintic, roots (warm from the previous epoch's roots when `warm`),
 // images, magnification. Updates z (the polynomial roots) and `warm`. The root iteration has a
 // single call site (a short job list: warm solve, cold retry, refinement next to the secondary)
 // so that the unrolled solver is emitted once per arithmetic.
+// `cubic` overrides the Aberth stop rule: the MIXED re-solve starts from FP32 roots (relative
+// error ~1e-6), so one cubic step already lands far below FP64 rounding.
 template <typename T>
 __device__ __forceinline__ EpochOut<T> solve_epoch(cx<T> zeta, T d, T q, cx<T> z[5], bool& warm,
-                                                   T* diag = nullptr) {
+                                                   T* diag = nullptr, T cubic = Tol<T>::cubic) {
     uint8_t extra = 0;
     if (norm2(zeta) < Tol<T>::shift * Tol<T>::shift ||
         norm2(mk<T>(zeta.re - d, zeta.im)) < Tol<T>::shift * Tol<T>::shift) {
@@ -372,7 +392,7 @@ __device__ __forceinline__ EpochOut<T> solve_epoch(cx<T> zeta, T d, T q, cx<T> z
     constexpr bool kTwoFrames = sizeof(T) == sizeof(float);
     const cx<T> dd = mk<T>(d, T(0));
     cx<T> c[6], wl[5];
-    int it = -1;
+    int it = -1, sweeps = 0;
     unsigned local = 0;
     // job 0: primary frame, warm if possible; job 1: primary frame, cold (only when job 0 was a
     // warm solve that failed); job 2: secondary frame for the roots next to the secondary
@@ -393,7 +413,8 @@ __device__ __forceinline__ EpochOut<T> solve_epoch(cx<T> zeta, T d, T q, cx<T> z
             mask = local;
             cap = Tol<T>::cap_warm;
         }
-        const int r = aberth(c, z, cap, mask);
+        const int r = aberth(c, z, cap, mask, cold ? Tol<T>::cubic : cubic);
+        sweeps += r < 0 ? cap : r;
         if (job == 2) {
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
@@ -417,7 +438,12 @@ __device__ __forceinline__ EpochOut<T> solve_epoch(cx<T> zeta, T d, T q, cx<T> z
         local = 0;
 #pragma unroll
         for (int i = 0; i < 5; ++i) local |= (norm2(z[i] - dd) < lim2 ? 1u : 0u) << i;
-        if (!local) break;
+        // a lone root next to the secondary is resolved in the primary frame; two or more are
+        // a cluster that only the secondary's frame resolves in FP32
+        if (__popc(local) < 2) {
+            local = 0;
+            break;
+        }
         job = 2;
     }
     warm = it >= 0;
@@ -430,6 +456,7 @@ __device__ __forceinline__ EpochOut<T> solve_epoch(cx<T> zeta, T d, T q, cx<T> z
     }
     EpochOut<T> o = select_images(rr, zeta, d, q, diag);
     o.flag |= extra | (it < 0 ? FLAG_CAP : 0);
+    o.sweeps = sweeps;
     return o;
 }
 

@@ -39,7 +39,17 @@ struct ForwardArgs {
     double* chi2_out = nullptr;    // optional [n_cand]; null -> no chi^2
     int mode = SBLM_FP64;
     int G = 32;                    // threads per candidate (power of two, <= 256)
+    // MIXED only: queue of epochs to re-solve in FP64 (capacity entries of
+    // deferred_entry_bytes() each) and its counter; launch_forward zeroes the counter
+    void* queue = nullptr;
+    unsigned* queue_count = nullptr;
+    unsigned queue_cap = 0;
 };
+
+// scratch of the MIXED re-solve queue: entry count sized for a few percent of the epochs (an
+// epoch that finds the queue full is re-solved in place, so the size is a speed choice only)
+unsigned mixed_queue_capacity(int n_cand, int n_ep);
+size_t deferred_entry_bytes();
 
 size_t staged_bytes(int mode, bool chi2, int n_ep);
 int choose_group(int n_cand, int n_ep);

@@ -76,6 +76,7 @@ _SIGS = {
     "sblm_ea_generation": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_ea_generation_noalloc": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_fit": (ctypes.c_int, [_p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p, _p]),
+    "sblm_peak_rates": (ctypes.c_int, [_p, _p, _p]),
     "sblm_fit_batch": (
         ctypes.c_int,
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p],
@@ -291,6 +292,13 @@ def fit_batch(t, flux, sigma, offsets, lo, hi, p, stream=None):
                              best.ctypes.data, best_chi2.ctypes.data, s)
     _check(st, "sblm_fit_batch")
     return best, best_chi2
+
+
+def peak_rates(stream=None):
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sblm_peak_rates(ctypes.byref(a), ctypes.byref(b), stream), "sblm_peak_rates")
+    return a.value, b.value
 
 
 def exported_symbols():
