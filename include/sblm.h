@@ -210,6 +210,12 @@ sblm_status sblm_fit(const double* t, const double* flux, const double* sigma, i
                      const sblm_bounds* bounds, const sblm_ea_params* params, double* best_theta,
                      double* best_chi2, double* trace, void* stream);
 
+/* Launch shape of the persistent batched fitter (sblm_autotune_batch picks one). */
+typedef struct {
+    int32_t group; /* threads per candidate: 1, 2, 4, 8, 16 or 32 (0: default 16) */
+    int32_t block; /* threads per block: a multiple of 32 up to 512 (0: default 512) */
+} sblm_batch_tuning;
+
 /*
  * Fit n_lc lightcurves of uneven length at once: lightcurve i owns epochs
  * [offsets[i], offsets[i+1]) of the concatenated t, flux, sigma arrays (offsets [n_lc + 1],
@@ -221,6 +227,32 @@ sblm_status sblm_fit_batch(const double* t, const double* flux, const double* si
                            const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
                            const sblm_ea_params* params, double* best_theta, double* best_chi2,
                            void* stream);
+
+/*
+ * sblm_fit_batch with an explicit launch shape (NULL: the defaults). Details of the batched
+ * fitter: one persistent block per SM takes lightcurves, longest first, from a work counter and
+ * runs every generation of one lightcurve's fit itself (the lightcurve staged in shared memory,
+ * so n_pop and the longest lightcurve must fit 200 KB of it: with n_pop = 1024 that is about
+ * 7,600 epochs in FP64 and 11,000 in FP32/MIXED; SBLM_EINVAL otherwise). The launch is captured in
+ * a CUDA graph the first time and replayed while every argument (pointers included) repeats.
+ * Results are those of sblm_fit on each lightcurve with stream id = the lightcurve's index,
+ * except that the evaluation's launch shape differs (chi^2 agree to rounding).
+ */
+sblm_status sblm_fit_batch_tuned(const double* t, const double* flux, const double* sigma,
+                                 const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                 const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                 double* best_theta, double* best_chi2, void* stream);
+
+/*
+ * Autotuner of the batched fitter (not part of the paper's method): times `trial_generations`
+ * generations of the given batch for each launch shape in {8, 16, 32} threads per candidate x
+ * {256, 512} threads per block and returns the fastest in *best (and its time in *best_ms, may
+ * be NULL). The Python binding keeps a JSON cache of the results keyed by the workload's shape.
+ */
+sblm_status sblm_autotune_batch(const double* t, const double* flux, const double* sigma,
+                                const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                const sblm_ea_params* params, int32_t trial_generations,
+                                sblm_batch_tuning* best, double* best_ms, void* stream);
 
 /*
  * Measured FMA throughput of the current device, in TFLOP/s (an FMA counts as 2 flop): eight

@@ -1,0 +1,419 @@
+// batch.cu -- sblm_fit_batch: many lightcurves of uneven length, each with its own population
+// and the whole evolutionary sequence of Appendix A, inside one persistent launch.
+//
+// One block per SM takes lightcurves from an atomic work counter, longest first (the host sorts
+// them), and runs every generation of that lightcurve's fit in the block: the lightcurve staged
+// in shared memory, the population's chi^2 by the same per-thread epoch runs as the forward
+// kernel (G threads per candidate, several passes over the population), MIXED re-solves of the
+// block's queue in a block-wide pass, then ranking, archive, stagnation, offspring or restart.
+// No block ever waits for another, so no wait can stall the GPU. The launch is captured once in
+// a CUDA graph and replayed for repeated calls with the same arguments.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "ea_launch.cuh"
+#include "forward_run.cuh"
+#include "runtime.cuh"
+
+namespace sblm {
+
+sblm_status check_bounds(const sblm_bounds* b, Bounds* out);
+
+namespace {
+
+constexpr int kBatchMaxThreads = 512;
+constexpr size_t kBatchSmemBudget = 200 * 1024;  // dynamic shared memory per block
+
+struct BatchArgs {
+    const double* t;
+    const double* flux;
+    const double* sigma;
+    const int64_t* offsets;
+    const int* order;  // lightcurves, longest first
+    int n_lc;
+    Bounds b;
+    EAConst c;  // stream is set per lightcurve
+    int n_gen;
+    int G;
+    int n2;            // power of two >= n_pop
+    double* P;         // per block: 2 x n_pop x 6
+    uint64_t* keys;    // per block: n_pop x 6
+    Deferred* queue;   // per block: qcap entries
+    unsigned qcap;
+    unsigned* next;    // work counter
+    double* best_theta;
+    double* best_chi2;
+    int max_ep;        // longest lightcurve the staging area holds
+};
+
+size_t batch_smem_bytes(int mode, int n_pop, int n2, int max_ep) {
+    const size_t ep = (size_t)max_ep * (mode == SBLM_FP64 ? 3 * sizeof(double) : sizeof(float4));
+    return ((ep + 15) & ~size_t(15)) + sizeof(double) * n_pop + (sizeof(double) + sizeof(int)) * n2;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_pop = a.c.n_pop, n_par = a.c.n_par, G = a.G;
+    const size_t ep_bytes =
+        ((size_t)a.max_ep * (MODE == SBLM_FP64 ? 3 * sizeof(double) : sizeof(float4)) + 15) & ~size_t(15);
+    double* s_chi = reinterpret_cast<double*>(smem + ep_bytes);
+    double* s_key = s_chi + n_pop;
+    int* s_idx = reinterpret_cast<int*>(s_key + a.n2);
+    __shared__ sblm_ea_state s_state;
+    __shared__ int s_job, s_restart;
+    __shared__ double s_pmut;
+    __shared__ unsigned s_qcount;
+
+    double* P0 = a.P + (size_t)blockIdx.x * 2 * n_pop * n_par;
+    double* Pb[2] = {P0, P0 + (size_t)n_pop * n_par};
+    uint64_t* keys = a.keys + (size_t)blockIdx.x * n_pop * n_par;
+    Deferred* queue = a.queue + (size_t)blockIdx.x * a.qcap;
+    const int m = n_pop * n_par;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_job = (int)atomicAdd(a.next, 1u);
+        __syncthreads();
+        const int job = s_job;
+        __syncthreads();
+        if (job >= a.n_lc) break;
+        const int lc = a.order[job];
+        const int64_t e_begin = a.offsets[lc];
+        const int n_ep = (int)(a.offsets[lc + 1] - e_begin);
+        const LCView view = stage_lightcurve<MODE, true>(smem, a.t + e_begin, a.flux + e_begin, a.sigma + e_begin, n_ep);
+        EAConst c = a.c;
+        c.stream = (uint64_t)lc;
+
+        // Appendix A, "Initialisation"
+        for (int e = threadIdx.x; e < m; e += blockDim.x) keys[e] = init_key(c, 0, (uint64_t)e);
+        __syncthreads();
+        block_init_values(c, 0, keys, m, Pb[0], 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key), a.n2);
+        if (threadIdx.x == 0) state_reset(c, s_state);
+        __syncthreads();
+
+        const int group = threadIdx.x / G, g = threadIdx.x % G;
+        const int per_pass = blockDim.x / G;
+        const int seg = (n_ep + G - 1) / G;
+        const int e0 = min(n_ep, g * seg), e1 = min(n_ep, e0 + seg);
+        int cur = 0;
+        for (int gen = 0; gen < a.n_gen; ++gen) {
+            // fitness of every row (decode + forward model + chi^2)
+            if (threadIdx.x == 0) s_qcount = 0;
+            __syncthreads();
+            for (int base = 0; base < n_pop; base += per_pass) {
+                const int cand = base + group;
+                const bool valid = cand < n_pop;
+                Cand k{};
+                if (valid) k = candidate<true>(Pb[cur], a.b, cand);
+                double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, nullptr, nullptr, queue,
+                                                        &s_qcount, a.qcap);
+                for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
+                if (g == 0 && valid) s_chi[cand] = chi;
+            }
+            __syncthreads();
+            if constexpr (MODE == SBLM_MIXED) {  // the block's queued epochs, in FP64
+                const unsigned n = min(s_qcount, a.qcap);
+                for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+                    const Deferred q = queue[i];
+                    const Cand k = candidate<true>(Pb[cur], a.b, q.c);
+                    const float4 ep = view.s_ep[q.e];
+                    const double term = resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w,
+                                                     nullptr, nullptr, q.e, true);
+                    atomicAdd(&s_chi[q.c], term);
+                }
+                __syncthreads();
+            }
+            // ranking, archive, stagnation
+            block_rank(s_chi, n_pop, a.n2, s_key, s_idx);
+            const bool produce = gen + 1 < a.n_gen;
+            if (threadIdx.x == 0) {
+                double p_used = 0.0;
+                s_restart = block_bookkeeping(c, gen, s_key[0], Pb[cur] + (size_t)s_idx[0] * n_par, s_state,
+                                              produce, &p_used);
+                s_pmut = p_used;
+            }
+            __syncthreads();
+            if (!produce) break;
+            double* next = Pb[cur ^ 1];
+            if (s_restart) {
+                for (int e = threadIdx.x; e < m; e += blockDim.x)
+                    keys[e] = init_key(c, (uint64_t)(gen + 1), (uint64_t)e);
+                __syncthreads();
+                block_init_values(c, gen + 1, keys, m, next, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
+                                  a.n2);
+            } else {
+                if (threadIdx.x == 0) {
+                    const double* e = Pb[cur] + (size_t)s_idx[0] * n_par;
+                    for (int j = 0; j < n_par; ++j) next[j] = e[j];
+                }
+                for (int k = threadIdx.x; k < n_pop / 2; k += blockDim.x)
+                    offspring_pair(c, gen, Pb[cur], s_idx, s_pmut, k, next);
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        if (threadIdx.x == 0) {
+            double av[SBLM_NPAR];
+            for (int j = 0; j < SBLM_NPAR; ++j) av[j] = a.b.lo[j] + (a.b.hi[j] - a.b.lo[j]) * s_state.best_genes[j];
+            double* th = a.best_theta + (size_t)lc * SBLM_NPAR;
+            for (int j = 0; j < 5; ++j) th[j] = av[j];
+            th[5] = exp10(av[5]);
+            a.best_chi2[lc] = s_state.best_chi2;
+        }
+        __syncthreads();
+    }
+}
+
+template <int MODE>
+cudaError_t launch_batch_mode(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s,
+                              bool attr_only) {
+    auto kern = batch_fit_kernel<MODE>;
+    if (attr_only) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// attr_only: set the shared-memory opt-in (done before a stream capture begins)
+cudaError_t launch_batch(int mode, const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s,
+                         bool attr_only) {
+    switch (mode) {
+        case SBLM_FP64: return launch_batch_mode<SBLM_FP64>(a, blocks, threads, smem, s, attr_only);
+        case SBLM_MIXED: return launch_batch_mode<SBLM_MIXED>(a, blocks, threads, smem, s, attr_only);
+        default: return launch_batch_mode<SBLM_FP32>(a, blocks, threads, smem, s, attr_only);
+    }
+}
+
+// The graph of the last call (counter reset + persistent kernel), replayed while the
+// arguments stay the same.
+struct GraphCache {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+};
+GraphCache g_graph;
+
+struct Prepared {
+    BatchArgs a;
+    int blocks, threads;
+    size_t smem;
+    int mode;
+};
+
+// validate, stage and lay out one batch call; on success `st` has begun
+sblm_status prepare(const double* t, const double* flux, const double* sigma, const int64_t* offsets, int32_t n_lc,
+                    const sblm_bounds* bounds, const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                    double* best_theta, double* best_chi2, Staging& st, int* i_th, int* i_c, Prepared* out) {
+    EAConst c;
+    SBLM_TRY(ea_const(params, params ? params->n_pop : 0, SBLM_NPAR, 0, &c));
+    if (params->n_gen < 1) return fail(SBLM_EINVAL, "n_gen must be >= 1");
+    if (n_lc < 1) return fail(SBLM_EINVAL, "n_lc must be >= 1");
+    if (!offsets || !best_theta || !best_chi2) return fail(SBLM_EINVAL, "offsets, best_theta and best_chi2 are required");
+    Bounds b;
+    SBLM_TRY(check_bounds(bounds, &b));
+    // offsets are needed on the host for the layout
+    std::vector<int64_t> off(n_lc + 1);
+    bool off_dev = false;
+    SBLM_TRY(is_device_pointer(offsets, &off_dev));
+    if (off_dev)
+        SBLM_CUDA(cudaMemcpy(off.data(), offsets, sizeof(int64_t) * (n_lc + 1), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(off.data(), offsets, sizeof(int64_t) * (n_lc + 1));
+    if (off[0] != 0) return fail(SBLM_EINVAL, "offsets[0] must be 0");
+    int max_ep = 0;
+    for (int i = 0; i < n_lc; ++i) {
+        const int64_t n = off[i + 1] - off[i];
+        if (n < 1) return fail(SBLM_EINVAL, "lightcurve %d has no epochs", i);
+        max_ep = (int)std::max<int64_t>(max_ep, n);
+    }
+    const int64_t total = off[n_lc];
+    const int mode = params->precision;
+    int G = tuning && tuning->group > 0 ? tuning->group : 16;
+    int threads = tuning && tuning->block > 0 ? tuning->block : 512;
+    if (G < 1 || G > 32 || (G & (G - 1))) return fail(SBLM_EINVAL, "tuning group must be a power of two <= 32");
+    if (threads < 32 || threads > kBatchMaxThreads || threads % 32)
+        return fail(SBLM_EINVAL, "tuning block must be a multiple of 32 in [32, %d]", kBatchMaxThreads);
+    int n2 = 1;
+    while (n2 < c.n_pop) n2 <<= 1;
+    const size_t smem = batch_smem_bytes(mode, c.n_pop, n2, max_ep);
+    if (smem > kBatchSmemBudget)
+        return fail(SBLM_EINVAL, "longest lightcurve (%d epochs) does not fit the %zu-byte staging area with n_pop=%d",
+                    max_ep, kBatchSmemBudget, c.n_pop);
+    int dev = 0, sms = 0;
+    SBLM_CUDA(cudaGetDevice(&dev));
+    SBLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = std::min(sms, n_lc);
+
+    int i_t, i_f, i_s, i_o;
+    SBLM_TRY(st.arg(t, sizeof(double) * total, true, false, &i_t));
+    SBLM_TRY(st.arg(flux, sizeof(double) * total, true, false, &i_f));
+    SBLM_TRY(st.arg(sigma, sizeof(double) * total, true, false, &i_s));
+    SBLM_TRY(st.arg(offsets, sizeof(int64_t) * (n_lc + 1), true, false, &i_o));
+    SBLM_TRY(st.arg(best_theta, sizeof(double) * 6 * (size_t)n_lc, false, true, i_th));
+    SBLM_TRY(st.arg(best_chi2, sizeof(double) * (size_t)n_lc, false, true, i_c));
+    bool d1, d2, d3;
+    SBLM_TRY(is_device_pointer(t, &d1));
+    SBLM_TRY(is_device_pointer(flux, &d2));
+    SBLM_TRY(is_device_pointer(sigma, &d3));
+    if (!d1 && !d2 && !d3) SBLM_TRY(check_lightcurve_host(t, flux, sigma, (int)total));
+    // per block: epochs past this are re-solved in place (a speed choice only)
+    const unsigned qcap = mode == SBLM_MIXED ? std::min(mixed_queue_capacity(c.n_pop, max_ep), 32768u) : 0;
+    const int k_order = st.scratch(sizeof(int) * n_lc);
+    const int k_P = st.scratch(sizeof(double) * 2 * (size_t)c.n_pop * SBLM_NPAR * blocks);
+    const int k_keys = st.scratch(sizeof(uint64_t) * (size_t)c.n_pop * SBLM_NPAR * blocks);
+    const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
+    const int k_next = st.scratch(sizeof(unsigned));
+    SBLM_TRY(st.begin());
+    // longest first (stable): the classic longest-processing-time order for the work queue
+    std::vector<int> order(n_lc);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return off[x + 1] - off[x] > off[y + 1] - off[y]; });
+    SBLM_CUDA(cudaMemcpyAsync(st.scratch_ptr(k_order), order.data(), sizeof(int) * n_lc, cudaMemcpyHostToDevice,
+                              st.stream()));
+    BatchArgs a{};
+    a.t = static_cast<const double*>(st.dev(i_t));
+    a.flux = static_cast<const double*>(st.dev(i_f));
+    a.sigma = static_cast<const double*>(st.dev(i_s));
+    a.offsets = static_cast<const int64_t*>(st.dev(i_o));
+    a.order = static_cast<const int*>(st.scratch_ptr(k_order));
+    a.n_lc = n_lc;
+    a.b = b;
+    a.c = c;
+    a.n_gen = params->n_gen;
+    a.G = G;
+    a.n2 = n2;
+    a.P = static_cast<double*>(st.scratch_ptr(k_P));
+    a.keys = static_cast<uint64_t*>(st.scratch_ptr(k_keys));
+    a.queue = static_cast<Deferred*>(st.scratch_ptr(k_q));
+    a.qcap = qcap;
+    a.next = static_cast<unsigned*>(st.scratch_ptr(k_next));
+    a.best_theta = static_cast<double*>(st.dev(*i_th));
+    a.best_chi2 = static_cast<double*>(st.dev(*i_c));
+    a.max_ep = max_ep;
+    out->a = a;
+    out->blocks = blocks;
+    out->threads = threads;
+    out->smem = smem;
+    out->mode = mode;
+    return SBLM_OK;
+}
+
+sblm_status run_graph(const Prepared& p, cudaStream_t s) {
+    // the cache key: every launch argument (the graph replays exactly this launch)
+    std::vector<unsigned char> key(sizeof(BatchArgs) + sizeof(int) * 3 + sizeof(size_t));
+    unsigned char* w = key.data();
+    std::memcpy(w, &p.a, sizeof(BatchArgs));
+    w += sizeof(BatchArgs);
+    std::memcpy(w, &p.blocks, sizeof(int));
+    std::memcpy(w + sizeof(int), &p.threads, sizeof(int));
+    std::memcpy(w + 2 * sizeof(int), &p.mode, sizeof(int));
+    std::memcpy(w + 3 * sizeof(int), &p.smem, sizeof(size_t));
+    int dev = 0;
+    SBLM_CUDA(cudaGetDevice(&dev));
+    key.insert(key.end(), reinterpret_cast<unsigned char*>(&dev), reinterpret_cast<unsigned char*>(&dev) + sizeof dev);
+    if (!g_graph.exec || g_graph.key != key) {
+        if (g_graph.exec) {
+            cudaGraphExecDestroy(g_graph.exec);
+            g_graph.exec = nullptr;
+        }
+        SBLM_CUDA(launch_batch(p.mode, p.a, p.blocks, p.threads, p.smem, s, true));
+        cudaStream_t cap;
+        SBLM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemsetAsync(p.a.next, 0, sizeof(unsigned), cap);
+            cudaError_t e2 = launch_batch(p.mode, p.a, p.blocks, p.threads, p.smem, cap, false);
+            e = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess && (e1 != cudaSuccess || e2 != cudaSuccess)) {
+                cudaGraphDestroy(graph);
+                e = e1 != cudaSuccess ? e1 : e2;
+            }
+        }
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return cuda_fail(e, "capturing the batched fit");
+        e = cudaGraphInstantiate(&g_graph.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g_graph.exec = nullptr;
+            return cuda_fail(e, "instantiating the batched fit graph");
+        }
+        g_graph.key = key;
+    }
+    SBLM_CUDA(cudaGraphLaunch(g_graph.exec, s));
+    return SBLM_OK;
+}
+
+}  // namespace
+}  // namespace sblm
+
+using namespace sblm;
+
+extern "C" sblm_status sblm_fit_batch_tuned(const double* t, const double* flux, const double* sigma,
+                                            const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                            const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                            double* best_theta, double* best_chi2, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    int i_th, i_c;
+    Prepared p;
+    SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, best_theta, best_chi2, st, &i_th, &i_c, &p));
+    SBLM_TRY(run_graph(p, s));
+    SBLM_TRY(st.end());
+    SBLM_CUDA(cudaStreamSynchronize(s));
+    return SBLM_OK;
+}
+
+extern "C" sblm_status sblm_fit_batch(const double* t, const double* flux, const double* sigma,
+                                      const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                      const sblm_ea_params* params, double* best_theta, double* best_chi2,
+                                      void* stream) {
+    return sblm_fit_batch_tuned(t, flux, sigma, offsets, n_lc, bounds, params, nullptr, best_theta, best_chi2,
+                                stream);
+}
+
+extern "C" sblm_status sblm_autotune_batch(const double* t, const double* flux, const double* sigma,
+                                           const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                           const sblm_ea_params* params, int32_t trial_generations,
+                                           sblm_batch_tuning* best, double* best_ms, void* stream) {
+    if (!params || !best) return fail(SBLM_EINVAL, "params and best are required");
+    if (trial_generations < 1) return fail(SBLM_EINVAL, "trial_generations must be >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    sblm_ea_params p = *params;
+    p.n_gen = trial_generations;
+    std::vector<double> th(6 * (size_t)n_lc), ch(n_lc);
+    const int groups[] = {8, 16, 32};
+    const int blocks[] = {256, 512};
+    double best_t = INFINITY;
+    sblm_batch_tuning best_cfg{16, 512};
+    for (int bl : blocks) {
+        for (int gr : groups) {
+            sblm_batch_tuning cfg{gr, bl};
+            // warm (builds the graph), then time one replay
+            SBLM_TRY(sblm_fit_batch_tuned(t, flux, sigma, offsets, n_lc, bounds, &p, &cfg, th.data(), ch.data(), stream));
+            cudaEvent_t e0, e1;
+            SBLM_CUDA(cudaEventCreate(&e0));
+            SBLM_CUDA(cudaEventCreate(&e1));
+            SBLM_CUDA(cudaEventRecord(e0, s));
+            SBLM_TRY(sblm_fit_batch_tuned(t, flux, sigma, offsets, n_lc, bounds, &p, &cfg, th.data(), ch.data(), stream));
+            SBLM_CUDA(cudaEventRecord(e1, s));
+            SBLM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SBLM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (ms < best_t) {
+                best_t = ms;
+                best_cfg = cfg;
+            }
+        }
+    }
+    *best = best_cfg;
+    if (best_ms) *best_ms = best_t;
+    return SBLM_OK;
+}

@@ -27,38 +27,17 @@ __global__ void init_keys_kernel(EAConst c, int gen, uint64_t* __restrict__ keys
     if (e < m) keys[e] = init_key(c, (uint64_t)gen, (uint64_t)e);
 }
 
-// Element e of the fresh population: its key's rank among all keys (counted against tiles of
-// the key array in shared memory) decides its pairing and value. Every thread of the block
-// takes part in the tile loads.
-__device__ void init_by_rank(const EAConst& c, int gen, const uint64_t* __restrict__ keys, int m,
-                             double* __restrict__ P) {
-    __shared__ uint64_t tile[kInitTile];
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t mine = e < m ? keys[e] : 0;
-    uint32_t pos = 0;
-    for (int base = 0; base < m; base += kInitTile) {
-        const int n = min(kInitTile, m - base);
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = keys[base + i];
-        __syncthreads();
-        if (e < m)
-            for (int i = 0; i < n; ++i) pos += tile[i] < mine;
-    }
-    if (e < m) P[e] = init_value(c, (uint64_t)gen, pos, (uint64_t)m);
-}
-
 __global__ void init_values_kernel(EAConst c, int gen, const uint64_t* __restrict__ keys, int m,
                                    double* __restrict__ P) {
-    init_by_rank(c, gen, keys, m, P);
+    __shared__ uint64_t tile[kInitTile];
+    block_init_values(c, gen, keys, m, P, blockIdx.x * blockDim.x, m, tile, kInitTile);
 }
 
 __global__ void state_reset_kernel(EAConst c, sblm_ea_state* state) {
     if (threadIdx.x != 0) return;
     sblm_ea_state s;
     memset(&s, 0, sizeof s);
-    s.p_mut = c.p_mut0;
-    s.best_chi2 = INFINITY;
-    for (int j = 0; j < SBLM_MAX_NPAR; ++j) s.best_genes[j] = NAN;
+    state_reset(c, s);
     *state = s;
 }
 
@@ -72,56 +51,18 @@ __global__ void __launch_bounds__(kRankThreads)
     double* skey = reinterpret_cast<double*>(smem);
     int* sidx = reinterpret_cast<int*>(skey + n2);
     __shared__ int s_restart;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        if (i < c.n_pop) {
-            const double v = chi2[i];
-            skey[i] = isnan(v) ? INFINITY : v;
-            sidx[i] = i;
-        } else {
-            skey[i] = INFINITY;
-            sidx[i] = 0x7fffffff;
-        }
-    }
-    __syncthreads();
-    // bitonic sort, ascending in (fitness, row)
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const bool greater = pair_less(skey[l], sidx[l], skey[i], sidx[i]);
-                    if (greater == up) {
-                        const double tk = skey[i];
-                        skey[i] = skey[l];
-                        skey[l] = tk;
-                        const int ti = sidx[i];
-                        sidx[i] = sidx[l];
-                        sidx[l] = ti;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
+    block_rank(chi2, c.n_pop, n2, skey, sidx);
     for (int i = threadIdx.x; i < c.n_pop; i += blockDim.x) order[i] = sidx[i];
     if (threadIdx.x == 0) {
         sblm_ea_state s = *state;
-        const double best = skey[0];
-        if (best < s.best_chi2) {
-            s.best_chi2 = best;
-            const double* row = P + (size_t)sidx[0] * c.n_par;
-            for (int j = 0; j < c.n_par; ++j) s.best_genes[j] = row[j];
-        }
-        const double p_used = s.p_mut;
-        int restart = 0;
-        if (produce) restart = stagnation_update(s, c, best);
-        s.generation = gen + 1;
+        double p_used = 0.0;
+        const int restart =
+            block_bookkeeping(c, gen, skey[0], P + (size_t)sidx[0] * c.n_par, s, produce != 0, &p_used);
         *state = s;
         ctrl->p_mut_used = p_used;
         ctrl->restart = restart;
         if (trace_row) {
-            trace_row[0] = best;
+            trace_row[0] = skey[0];
             trace_row[1] = p_used;
             trace_row[2] = (double)s.n_restarts;
             trace_row[3] = s.best_chi2;
@@ -139,36 +80,17 @@ __global__ void offspring_kernel(EAConst c, int gen, const double* __restrict__ 
                                  const EACtrl* __restrict__ ctrl, const uint64_t* __restrict__ keys,
                                  double* __restrict__ P_next) {
     if (ctrl->restart) {  // uniform over the grid
-        init_by_rank(c, gen + 1, keys, c.n_pop * c.n_par, P_next);
+        __shared__ uint64_t tile[kInitTile];
+        const int m = c.n_pop * c.n_par;
+        block_init_values(c, gen + 1, keys, m, P_next, blockIdx.x * blockDim.x, m, tile, kInitTile);
         return;
     }
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n_par = c.n_par;
     if (k == 0) {  // elitism: the fittest row survives unmutated
-        const double* e = P + (size_t)order[0] * n_par;
-        for (int j = 0; j < n_par; ++j) P_next[j] = e[j];
+        const double* e = P + (size_t)order[0] * c.n_par;
+        for (int j = 0; j < c.n_par; ++j) P_next[j] = e[j];
     }
-    const int n_pairs = c.n_pop / 2;  // ceil((N_pop - 1) / 2)
-    if (k >= n_pairs) return;
-    const uint64_t g = (uint64_t)gen;
-    const int ra = tournament(c, g, 2 * (uint64_t)k);
-    const int rb = tournament(c, g, 2 * (uint64_t)k + 1);
-    const double* pa = P + (size_t)order[ra] * n_par;
-    const double* pb = P + (size_t)order[rb] * n_par;
-    const uint32_t mode = uniform_int(philox4x64(g, OP_MODE, (uint64_t)k, 0, c.seed, c.stream).x[0], 3u);
-    const int row1 = 1 + 2 * k, row2 = 2 + 2 * k;
-    const double p_mut = ctrl->p_mut_used;
-    for (int j = 0; j < n_par; ++j) {
-        const uint64_t w = philox4x64(g, OP_F, (uint64_t)k, (uint64_t)j, c.seed, c.stream).x[0];
-        const double f = mode == 0 ? u01(w) : (mode == 1 ? (double)top_bit(w) : 1.0);
-        const double omf = __dsub_rn(1.0, f);
-        const double a = pa[j], b = pb[j];
-        const double c1 = __dadd_rn(__dmul_rn(a, f), __dmul_rn(b, omf));
-        const double c2 = __dadd_rn(__dmul_rn(b, f), __dmul_rn(a, omf));
-        P_next[(size_t)row1 * n_par + j] = mutate_gene(c, g, (uint64_t)row1, (uint64_t)j, c1, p_mut);
-        if (row2 < c.n_pop)
-            P_next[(size_t)row2 * n_par + j] = mutate_gene(c, g, (uint64_t)row2, (uint64_t)j, c2, p_mut);
-    }
+    if (k < c.n_pop / 2) offspring_pair(c, gen, P, order, ctrl->p_mut_used, k, P_next);  // ceil((N_pop-1)/2)
 }
 
 int blocks_for(int n, int b) { return (n + b - 1) / b; }

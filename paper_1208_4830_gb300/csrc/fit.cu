@@ -121,12 +121,3 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     SBLM_CUDA(cudaStreamSynchronize(s));
     return SBLM_OK;
 }
-
-extern "C" sblm_status sblm_fit_batch(const double* t, const double* flux, const double* sigma,
-                                      const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
-                                      const sblm_ea_params* params, double* best_theta, double* best_chi2,
-                                      void* stream) {
-    (void)t; (void)flux; (void)sigma; (void)offsets; (void)n_lc; (void)bounds; (void)params;
-    (void)best_theta; (void)best_chi2; (void)stream;
-    return fail(SBLM_EINVAL, "sblm_fit_batch: not available in this build");
-}

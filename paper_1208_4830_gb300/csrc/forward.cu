@@ -8,8 +8,8 @@
 #include <algorithm>
 #include <cmath>
 
-#include "forward.cuh"
 #include "forward_launch.cuh"
+#include "forward_run.cuh"
 #include "runtime.cuh"
 
 namespace sblm {
@@ -17,55 +17,6 @@ namespace sblm {
 namespace {
 
 constexpr int kBlock = 256;
-
-template <bool FROM_GENES>
-__device__ __forceinline__ Cand candidate(const double* __restrict__ src, const Bounds& b, int c) {
-    if (!FROM_GENES) return load_cand(src, c);
-    // Eq. (EMMA-encoding): a_j = lo_j + (hi_j - lo_j) p_j; gene 5 is log10 q
-    const double* p = src + 6 * (size_t)c;
-    double a[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) a[j] = b.lo[j] + (b.hi[j] - b.lo[j]) * p[j];
-    Cand k;
-    k.t0 = a[0];
-    k.inv_tE = 1.0 / a[1];
-    k.u0 = a[2];
-    sincos(a[3], &k.sa, &k.ca);
-    k.d = a[4];
-    k.q = exp10(a[5]);
-    return k;
-}
-
-// s + x as an unevaluated pair (hi, lo) of floats: Knuth's two-sum, then renormalisation
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
-    const float s = hi + x;
-    const float v = s - hi;
-    const float e = (hi - (s - v)) + (x - v);
-    const float t = lo + e;
-    hi = s + t;
-    lo = t - (hi - s);
-}
-
-// the MIXED re-solve's Aberth stop rule (relative correction), see solve_epoch
-constexpr double kResolveCubic = 1e-6;
-
-// FP64 re-solve of one deferred epoch (MIXED), warm-started from its FP32 roots; returns the
-// chi^2 term. Out of line: an FP32 lane that must do it in place keeps its state on the stack
-// instead of competing with the FP64 solver for registers.
-__device__ __noinline__ double resolve_fp64(const cx<float>* z32, uint32_t why, const Cand* kk, double te,
-                                            double fe, double we, double* A_out, uint8_t* flags, size_t idx,
-                                            bool chi2) {
-    cx<double> zz[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) zz[i] = mk<double>(z32[i].re, z32[i].im);
-    bool w2 = true;
-    const EpochOut<double> o2 = solve_epoch<double>(zeta64(*kk, te), kk->d, kk->q, zz, w2, nullptr, kResolveCubic);
-    if (A_out) A_out[idx] = o2.A;
-    if (flags) flags[idx] = (uint8_t)(o2.flag | FLAG_FP64 | why);
-    if (!chi2) return 0.0;
-    const double r = (fe - o2.A) * we;
-    return r * r;
-}
 
 // MIXED, second pass: the queued epochs in full warps over the whole GPU. Each chi^2 term is
 // added atomically to its candidate's FP32 partial sum, so the summation order of these terms
@@ -85,8 +36,8 @@ __global__ void __launch_bounds__(256) resolve_kernel(const double* __restrict__
         const Cand k = candidate<FROM_GENES>(src, bounds, q.c);
         const double fe = CHI2 ? flux[q.e] : 0.0;
         const double we = CHI2 ? 1.0 / sigma[q.e] : 0.0;
-        const double term =
-            resolve_fp64(q.z, q.why, &k, t[q.e], fe, we, A_out, flags, (size_t)q.c * n_ep + q.e, CHI2);
+        const double term = resolve_fp64(q.z, q.why, &k, t[q.e], fe, we, A_out ? A_out + (size_t)q.c * n_ep : nullptr,
+                                         flags ? flags + (size_t)q.c * n_ep : nullptr, q.e, CHI2);
         if (CHI2) atomicAdd(&chi2_out[q.c], term);
     }
 }
@@ -102,134 +53,20 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
                                                          Deferred* __restrict__ queue,
                                                          unsigned* __restrict__ queue_count, unsigned queue_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
-    // staged lightcurve: FP64 mode keeps (t, F, 1/sigma) in FP64; the FP32 modes keep
-    // (t_hi, t_lo, F, 1/sigma) as floats, t = t_hi + t_lo split so that t - t0 stays exact
-    double* s_t = reinterpret_cast<double*>(smem);
-    double* s_f = s_t + (STAGED && MODE == SBLM_FP64 ? n_ep : 0);
-    double* s_w = s_f + (STAGED && MODE == SBLM_FP64 && CHI2 ? n_ep : 0);
-    float4* s_ep = reinterpret_cast<float4*>(smem);
-    if (STAGED) {
-        for (int e = threadIdx.x; e < n_ep; e += blockDim.x) {
-            const double te = t[e];
-            const double fe = CHI2 ? flux[e] : 0.0;
-            const double we = CHI2 ? 1.0 / sigma[e] : 0.0;
-            if (MODE == SBLM_FP64) {
-                s_t[e] = te;
-                if (CHI2) {
-                    s_f[e] = fe;
-                    s_w[e] = we;
-                }
-            } else {
-                const float th = (float)te;
-                s_ep[e] = make_float4(th, (float)(te - (double)th), (float)fe, (float)we);
-            }
-        }
-        __syncthreads();
-    }
+    const LCView lc = STAGED ? stage_lightcurve<MODE, CHI2>(smem, t, flux, sigma, n_ep)
+                             : LCView{t, flux, sigma, nullptr, nullptr, nullptr, nullptr};
     const int group = threadIdx.x / G, g = threadIdx.x % G;
     const int per_block = blockDim.x / G;
     const int c = blockIdx.x * per_block + group;
     const bool valid = c < n_cand;
     const int seg = (n_ep + G - 1) / G;
     const int e0 = min(n_ep, g * seg), e1 = min(n_ep, e0 + seg);
-    double chi = 0.0;
     Cand k{};
     if (valid) k = candidate<FROM_GENES>(src, bounds, c);
     double* A_row = (A_out && valid) ? A_out + (size_t)c * n_ep : nullptr;
     uint8_t* f_row = (flags && valid) ? flags + (size_t)c * n_ep : nullptr;
-    if constexpr (MODE == SBLM_FP64) {
-        cx<double> z[5];
-        bool warm = false;
-        for (int e = e0; valid && e < e1; ++e) {
-            const double te = STAGED ? s_t[e] : t[e];
-            const EpochOut<double> o = solve_epoch<double>(zeta64(k, te), k.d, k.q, z, warm);
-            if (A_row) A_row[e] = o.A;
-            if (f_row) f_row[e] = o.flag;
-            if (CHI2) {
-                const double fe = STAGED ? s_f[e] : flux[e];
-                const double we = STAGED ? s_w[e] : 1.0 / sigma[e];
-                const double r = (fe - o.A) * we;
-                chi += r * r;
-            }
-        }
-    } else {
-        const float t0h = (float)k.t0, t0l = (float)(k.t0 - (double)t0h);
-        const float itE = (float)k.inv_tE, sa = (float)k.sa, ca = (float)k.ca, u0 = (float)k.u0;
-        const float d = (float)k.d, q = (float)k.q;
-        const unsigned lane = threadIdx.x & 31u;
-        // per-thread chi^2 of the FP32 epochs as an unevaluated float pair (hi + lo): FP64-grade
-        // accumulation on the FP32 pipes; converted to FP64 for the cross-thread reduction
-        float chi_hi = 0.f, chi_lo = 0.f;
-        cx<float> z[5];
-        bool warm = false;
-        for (int it = 0; it < seg; ++it) {
-            const int e = e0 + it;
-            const bool act = valid && e < e1;
-            bool defer = false;
-            uint8_t why = 0;
-            if (act) {
-                float4 ep;
-                if (STAGED) {
-                    ep = s_ep[e];
-                } else {
-                    const double te = t[e];
-                    const float th = (float)te;
-                    ep = make_float4(th, (float)(te - (double)th), CHI2 ? (float)flux[e] : 0.f,
-                                     CHI2 ? (float)(1.0 / sigma[e]) : 0.f);
-                }
-                const float tau = diff_ff(ep.x, ep.y, t0h, t0l) * itE;
-                const cx<float> zeta = mk<float>(tau * sa + u0 * ca, -tau * ca + u0 * sa);
-                EpochOut<float> o = solve_epoch<float>(zeta, d, q, z, warm);
-                o.flag |= (o.min_det < kMixedDetTrigger ? FLAG_NEAR_DET : 0) |
-                          (o.min_gap < kMixedGapTrigger ? FLAG_NEAR_GAP : 0);
-                if (MODE == SBLM_MIXED) defer = o.flag != 0;
-                why = o.flag;
-                if (A_row) A_row[e] = o.A;
-                if (f_row) f_row[e] = o.flag;
-                if (CHI2 && !defer) {
-                    const float r = (ep.z - o.A) * ep.w;
-                    ff_add(chi_hi, chi_lo, r * r);
-                }
-            }
-            if constexpr (MODE == SBLM_MIXED) {
-                // one atomic per warp reserves queue slots for the lanes that defer
-                const unsigned b = __ballot_sync(0xffffffffu, defer);
-                if (b) {
-                    const int leader = __ffs(b) - 1;
-                    unsigned base = 0;
-                    if ((int)lane == leader) base = atomicAdd(queue_count, (unsigned)__popc(b));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (defer) {
-                        const unsigned slot = base + __popc(b & ((1u << lane) - 1u));
-                        if (slot < queue_cap) {
-                            Deferred& q = queue[slot];
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) q.z[i] = z[i];
-                            q.c = c;
-                            q.e = e;
-                            q.why = why;
-                        } else {  // queue full: re-solve here
-                            double te, fe = 0.0, we = 0.0;
-                            if (STAGED) {
-                                const float4 ep = s_ep[e];
-                                te = (double)ep.x + (double)ep.y;
-                                fe = ep.z;
-                                we = ep.w;
-                            } else {
-                                te = t[e];
-                                if (CHI2) {
-                                    fe = flux[e];
-                                    we = 1.0 / sigma[e];
-                                }
-                            }
-                            chi += resolve_fp64(z, why, &k, te, fe, we, A_out, flags, (size_t)c * n_ep + e, CHI2);
-                        }
-                    }
-                }
-            }
-        }
-        chi += (double)chi_hi + (double)chi_lo;
-    }
+    double chi = eval_run<MODE, CHI2, STAGED>(k, valid, c, e0, e1, seg, lc, A_row, f_row, queue, queue_count,
+                                              queue_cap);
     if (!CHI2) return;
     // deterministic reduction over the candidate's G threads
     const int width = min(G, 32);

@@ -62,6 +62,10 @@ class EAState(ctypes.Structure):
     ]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("block", ctypes.c_int32)]
+
+
 _p = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _u64 = ctypes.c_uint64
@@ -77,6 +81,15 @@ _SIGS = {
     "sblm_ea_generation_noalloc": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_fit": (ctypes.c_int, [_p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p, _p]),
     "sblm_peak_rates": (ctypes.c_int, [_p, _p, _p]),
+    "sblm_fit_batch_tuned": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p, _p, _p],
+    ),
+    "sblm_autotune_batch": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _i32, ctypes.POINTER(BatchTuning),
+         ctypes.POINTER(ctypes.c_double), _p],
+    ),
     "sblm_fit_batch": (
         ctypes.c_int,
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p],
@@ -280,18 +293,71 @@ def fit(t, flux, sigma, lo, hi, p, trace=False, stream=None):
     return (best, float(best_chi2[0]), tr) if trace else (best, float(best_chi2[0]))
 
 
-def fit_batch(t, flux, sigma, offsets, lo, hi, p, stream=None):
-    """Best theta [n_lc, 6] and chi^2 [n_lc] of lightcurves concatenated at ``offsets`` [n_lc + 1]."""
+def fit_batch(t, flux, sigma, offsets, lo, hi, p, tuning=None, stream=None):
+    """Best theta [n_lc, 6] and chi^2 [n_lc] of lightcurves concatenated at ``offsets`` [n_lc + 1]
+    (int64). ``tuning``: a BatchTuning, a (group, block) pair, "auto" (the cached autotuner result
+    for this workload's shape, tuned on first use) or None (the library's defaults)."""
     n_lc = int(offsets.shape[0]) - 1
     b = bounds(lo, hi)
     best = np.empty((n_lc, 6))
     best_chi2 = np.empty(n_lc)
+    if isinstance(tuning, str) and tuning == "auto":
+        tuning = autotune_batch(t, flux, sigma, offsets, lo, hi, p, stream=stream)
+    if isinstance(tuning, tuple):
+        tuning = BatchTuning(*tuning)
     a = [_ptr(x) for x in (t, flux, sigma, offsets)]
     s = _stream(stream, t, flux, sigma)
-    st = _lib.sblm_fit_batch(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p),
-                             best.ctypes.data, best_chi2.ctypes.data, s)
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    st = _lib.sblm_fit_batch_tuned(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p), tp,
+                                   best.ctypes.data, best_chi2.ctypes.data, s)
     _check(st, "sblm_fit_batch")
     return best, best_chi2
+
+
+TUNE_CACHE = os.environ.get("SBLM_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "sblm_tune.json"))
+
+
+def _tune_key(offsets, p):
+    import json
+
+    off = np.asarray(offsets.cpu() if hasattr(offsets, "cpu") else offsets)
+    n = np.diff(off)
+    return json.dumps({"n_lc": int(n.size), "max_ep": int(2 ** np.ceil(np.log2(max(1, n.max())))),
+                       "mean_ep": int(round(n.mean(), -2)), "n_pop": int(p.n_pop), "precision": int(p.precision)},
+                      sort_keys=True)
+
+
+def autotune_batch(t, flux, sigma, offsets, lo, hi, p, trial_generations=2, stream=None, cache=TUNE_CACHE):
+    """The fastest launch shape of the batched fitter for this workload's shape (times a few
+    generations of each candidate shape on the device); results persist in a JSON file."""
+    import json
+
+    key = _tune_key(offsets, p)
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            table = json.load(open(cache))
+        except (OSError, ValueError):
+            table = {}
+    if key in table:
+        return BatchTuning(*table[key]["tuning"])
+    n_lc = int(offsets.shape[0]) - 1
+    b = bounds(lo, hi)
+    best = BatchTuning()
+    ms = ctypes.c_double()
+    a = [_ptr(x) for x in (t, flux, sigma, offsets)]
+    s = _stream(stream, t, flux, sigma)
+    st = _lib.sblm_autotune_batch(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p),
+                                  trial_generations, ctypes.byref(best), ctypes.byref(ms), s)
+    _check(st, "sblm_autotune_batch")
+    table[key] = {"tuning": [best.group, best.block], "ms": ms.value, "trial_generations": trial_generations}
+    if cache:
+        try:
+            os.makedirs(os.path.dirname(cache), exist_ok=True)
+            json.dump(table, open(cache, "w"), indent=1, sort_keys=True)
+        except OSError:
+            pass
+    return best
 
 
 def peak_rates(stream=None):

@@ -132,3 +132,47 @@ def forward_sweep(n_cand=4096, n_ep=2000, seed=0, caustic_frac=0.1):
     truth = prior_theta(1, seed + 3)[0]
     z = _rng(seed + 4).standard_normal(n_ep)
     return Sweep(theta=theta, forced=forced, t=t, truth=truth, z=z, sigma_frac=0.01)
+
+
+@dataclass
+class Batch:
+    t: np.ndarray           # concatenated epochs
+    z: np.ndarray           # unit-normal noise draws, one per epoch
+    sigma_frac: np.ndarray  # per-epoch sigma as a fraction of the true flux
+    offsets: np.ndarray     # int64 [n_lc + 1]
+    truth: np.ndarray       # (n_lc, 6)
+
+    def observe(self, A_true):
+        """Observed flux and sigma from the truths' magnifications (concatenated)."""
+        sigma = self.sigma_frac * A_true
+        return A_true + sigma * self.z, sigma
+
+
+def seasonal_batch(n_lc=512, seed=0, n_min=200, n_max=5000, span=(-300.0, 300.0), season=245.0, gap=120.0,
+                   sig_lo=0.005, sig_hi=0.05):
+    """Lightcurves of uneven length with seasonal gaps: epoch counts uniform in [n_min, n_max];
+    epochs uniform inside observing seasons of `season` days separated by `gap`-day gaps (random
+    phase) within `span`; per-point sigma uniform in [sig_lo, sig_hi] of the true flux; truths
+    from the sweep priors. A lightcurve with no epoch inside |t - t0| < tE is redrawn."""
+    g = _rng(seed)
+    ts, zs, ss, offs, truths = [], [], [], [0], []
+    period = season + gap
+    while len(truths) < n_lc:
+        th = prior_theta(1, int(g.integers(0, 2**62)))[0]
+        n = int(g.integers(n_min, n_max + 1))
+        phase = g.uniform(0.0, period)
+        t = np.empty(0)
+        while t.size < n:
+            x = g.uniform(span[0], span[1], 2 * n)
+            x = x[np.mod(x - span[0] + phase, period) < season]
+            t = np.concatenate([t, x])
+        t = np.sort(t[:n])
+        if not np.any(np.abs(t - th[0]) < th[1]):
+            continue
+        ts.append(t)
+        zs.append(g.standard_normal(n))
+        ss.append(g.uniform(sig_lo, sig_hi, n))
+        offs.append(offs[-1] + n)
+        truths.append(th)
+    return Batch(t=np.concatenate(ts), z=np.concatenate(zs), sigma_frac=np.concatenate(ss),
+                 offsets=np.array(offs, dtype=np.int64), truth=np.array(truths))
