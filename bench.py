@@ -42,7 +42,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # ncu thread-level instruction counts (FMA counted as 2 flop), and the kernel's DRAM bytes per
 # launch, from the captures summarised in profiles/forward_kernel_<precision>_sweep_4096x2000.md
 PROFILE = {
-    "mixed": {"flop_per_mag": 3344.0, "traffic": 4.07e6, "file": "profiles/forward_kernel_mixed_sweep_4096x2000.md"},
+    "mixed": {"flop_per_mag": 2573.0, "traffic": 3.84e6, "file": "profiles/forward_kernel_mixed_sweep_4096x2000.md"},
 }
 
 
@@ -173,6 +173,8 @@ def run_gpu(args):
         m = e0.elapsed_time(e1) / n
         by_prec[prec] = {"ms_per_step": m, "value": N_CAND * N_EP / m * 1e3}
 
+    fits = run_fits(sblm, args) if (args.extras and args.fits) else None
+
     if rank == 0:
         value = world * N_CAND * N_EP / step_ms * 1e3
         fwd = float(np.mean(fwd_ms))
@@ -188,12 +190,14 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "candidates": N_CAND, "epochs": N_EP,
                        "precision": args.precision, "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replica x{world}" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "forward_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": "forward model pass (forward_kernel + MIXED resolve_kernel)",
+                         "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                          "traffic": prof.get("traffic"), "kernel_ms": fwd,
                          "flop_per_magnification": flop, "profile": prof.get("file"),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal unit counts and clock)"},
             "by_precision": by_prec,
+            "fits": fits,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
@@ -237,6 +241,40 @@ def make_device_step(sblm, P_in, t, flux, sigma, precision, dev):
         sblm.ea_generation(P_out, chi, p, 0, 0, state)
 
     return step
+
+
+FIT_LCS, FIT_POP, FIT_GEN = 32, 512, 150
+
+
+def run_fits(sblm, args):
+    """Fits per second of the persistent batched fitter on seasonal lightcurves, MIXED against
+    the plain FP64 EA on the same GPU, and the share of fits within delta chi^2 <= 1 of the
+    injected truth (the truth's chi^2 computed by the library in FP64)."""
+    import torch
+
+    from paper_1208_4830_gb300 import synth
+
+    b = synth.seasonal_batch(FIT_LCS, seed=11, n_min=200, n_max=400, span=(-100.0, 100.0), season=80.0, gap=30.0)
+    A = np.concatenate([sblm.magnification(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]], "fp64")[0]
+                        for i in range(FIT_LCS)])
+    flux, sigma = b.observe(A)
+    chi_true = np.array([sblm.chi2(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]],
+                                   flux[b.offsets[i] : b.offsets[i + 1]], sigma[b.offsets[i] : b.offsets[i + 1]],
+                                   "fp64")[0] for i in range(FIT_LCS)])
+    dev = [torch.tensor(x, device="cuda") for x in (b.t, flux, sigma, b.offsets)]
+    out = {"workload": f"{FIT_LCS} seasonal lightcurves, 200-400 epochs, sigma 0.5-5%, "
+                       f"N_pop {FIT_POP} x {FIT_GEN} generations, batched persistent fitter"}
+    for prec in ("mixed", "fp64"):
+        p = sblm.params(n_pop=FIT_POP, n_gen=FIT_GEN, precision=prec, seed=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, chi = sblm.fit_batch(*dev, synth.FIT_LO, synth.FIT_HI, p)
+        dt = time.perf_counter() - t0
+        out[prec] = {"fits_per_s": FIT_LCS / dt, "seconds": dt,
+                     "success": float(np.mean(chi - chi_true <= 1.0)),
+                     "magnifications_per_s": FIT_POP * FIT_GEN * float(b.t.size) / dt}
+    out["speedup_mixed_over_fp64"] = out["mixed"]["fits_per_s"] / out["fp64"]["fits_per_s"]
+    return out
 
 
 def run_e2e(sblm, sw, P0, flux, sigma, args):
@@ -344,6 +382,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-fits", dest="fits", action="store_false", help="skip the fits/s measurement")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the end-to-end and other-precision measurements (profiling runs)")
     args = ap.parse_args()

@@ -2,6 +2,7 @@
 // device. Per generation: the forward model over the population (all SMs), then the ranking
 // block and the offspring kernel; the host only enqueues.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "ea_launch.cuh"
@@ -21,6 +22,28 @@ __global__ void finish_kernel(const sblm_ea_state* __restrict__ state, Bounds b,
     for (int j = 0; j < 5; ++j) theta[j] = a[j];
     theta[5] = exp10(a[5]);
     *chi2 = state->best_chi2;
+}
+
+// cache key of a single-lightcurve fit: every value its launches depend on, field by field
+template <typename V>
+void put(std::vector<unsigned char>& k, const V& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), p, p + sizeof(V));
+}
+
+std::vector<unsigned char> fit_graph_key(const EAConst& c, const ForwardArgs& fa, int n_gen, const double* tr,
+                                         const double* th, const double* chi, const double* P0) {
+    std::vector<unsigned char> k;
+    put(k, c.n_pop), put(k, c.n_par), put(k, c.n_tourn), put(k, c.stag_window), put(k, c.restart_after);
+    put(k, c.p_mut0), put(k, c.stag_rel), put(k, c.seed), put(k, c.stream);
+    put(k, fa.t), put(k, fa.flux), put(k, fa.sigma), put(k, fa.n_ep), put(k, fa.n_cand), put(k, fa.mode);
+    put(k, fa.G), put(k, fa.chi2_out), put(k, fa.queue), put(k, fa.queue_count), put(k, fa.queue_cap);
+    for (int j = 0; j < SBLM_NPAR; ++j) put(k, fa.bounds.lo[j]), put(k, fa.bounds.hi[j]);
+    put(k, n_gen), put(k, tr), put(k, th), put(k, chi), put(k, P0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    put(k, dev);
+    return k;
 }
 
 }  // namespace
@@ -102,21 +125,33 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     fa.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
     fa.queue_cap = qcap;
 
-    SBLM_CUDA(launch_init(c, 0, keys, P[0], s));
-    SBLM_CUDA(launch_state_reset(c, state, s));
-    int cur = 0;
-    for (int g = 0; g < n_gen; ++g) {
-        fa.src = P[cur];
-        SBLM_CUDA(launch_forward(fa, s));
-        const bool produce = g + 1 < n_gen;
-        SBLM_CUDA(launch_rank(c, g, chi, P[cur], state, order, ctrl, keys, tr ? tr + 4 * (size_t)g : nullptr, produce,
-                              s));
-        if (produce) {
-            SBLM_CUDA(launch_offspring(c, g, P[cur], order, ctrl, keys, P[cur ^ 1], s));
-            cur ^= 1;
+    double* th_out = static_cast<double*>(st.dev(i_th));
+    double* chi_out = static_cast<double*>(st.dev(i_c));
+    // the whole sequence: ~3 launches per generation, captured once into a CUDA graph and
+    // replayed while the arguments repeat (the host only launches the graph)
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = launch_init(c, 0, keys, P[0], q);
+        if (e == cudaSuccess) e = launch_state_reset(c, state, q);
+        int cur = 0;
+        for (int g = 0; g < n_gen && e == cudaSuccess; ++g) {
+            fa.src = P[cur];
+            e = launch_forward(fa, q);
+            const bool produce = g + 1 < n_gen;
+            if (e == cudaSuccess)
+                e = launch_rank(c, g, chi, P[cur], state, order, ctrl, keys, tr ? tr + 4 * (size_t)g : nullptr,
+                                produce, q);
+            if (e == cudaSuccess && produce) {
+                e = launch_offspring(c, g, P[cur], order, ctrl, keys, P[cur ^ 1], q);
+                cur ^= 1;
+            }
         }
-    }
-    finish_kernel<<<1, 32, 0, s>>>(state, b, static_cast<double*>(st.dev(i_th)), static_cast<double*>(st.dev(i_c)));
+        if (e == cudaSuccess) {
+            finish_kernel<<<1, 32, 0, q>>>(state, b, th_out, chi_out);
+            e = cudaGetLastError();
+        }
+        return e;
+    };
+    SBLM_TRY(run_cached_graph(fit_graph_key(c, fa, n_gen, tr, th_out, chi_out, P[0]), enqueue, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));
     return SBLM_OK;

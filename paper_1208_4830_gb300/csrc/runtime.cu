@@ -143,6 +143,60 @@ sblm_status Staging::end() {
     return SBLM_OK;
 }
 
+namespace {
+struct CachedGraph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+};
+std::vector<CachedGraph>& graph_cache() {
+    static auto* v = new std::vector<CachedGraph>();
+    return *v;
+}
+constexpr size_t kGraphCacheSize = 8;
+}  // namespace
+
+sblm_status run_cached_graph(const std::vector<unsigned char>& key,
+                             const std::function<cudaError_t(cudaStream_t)>& enqueue, cudaStream_t s) {
+    auto& cache = graph_cache();
+    for (size_t i = 0; i < cache.size(); ++i) {
+        if (cache[i].key == key) {
+            SBLM_CUDA(cudaGraphLaunch(cache[i].exec, s));
+            return SBLM_OK;
+        }
+    }
+    // kernels that opt in to more shared memory set their attribute on the first launch; run the
+    // launches once on the caller's stream (this is also the first execution), then capture
+    SBLM_CUDA(enqueue(s));
+    cudaStream_t cap;
+    SBLM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t e1 = enqueue(cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return SBLM_OK;  // the launches already ran directly; no graph for this key
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SBLM_OK;
+    }
+    if (cache.size() >= kGraphCacheSize) {
+        cudaGraphExecDestroy(cache.front().exec);
+        cache.erase(cache.begin());
+    }
+    cache.push_back({key, exec});
+    return SBLM_OK;
+}
+
 }  // namespace sblm
 
 extern "C" {

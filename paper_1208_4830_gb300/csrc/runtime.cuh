@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "../../include/sblm.h"
@@ -81,6 +82,13 @@ class Staging {
     Scratch scratch_;
     std::vector<A> args_;
 };
+
+// Runs `enqueue` through a CUDA graph: the first call with a given key captures its launches
+// (on a private stream) and instantiates them; later calls with the same key replay the graph on
+// `s`. The last few graphs are kept. Kernel attributes that enqueue sets are set before capture
+// by a dry pass only if the caller did so itself; enqueue must only enqueue stream work.
+sblm_status run_cached_graph(const std::vector<unsigned char>& key,
+                             const std::function<cudaError_t(cudaStream_t)>& enqueue, cudaStream_t s);
 
 // Serialises calls that use a workspace (the lock is per process; calls are short to enqueue).
 struct CallLock {
