@@ -15,6 +15,10 @@ Modules
             every stochastic EA operator on both sides.
 ``ea``      the evolutionary algorithm of Appendix A, operator by operator, in the
             paper's order, plus a reference driver.
+``cnn``     the learned proposal network (not in the paper: this project's seeding of the
+            initial population), forward and backward by hand in FP64.
+``proposal`` the proposal's data path: training curves, binning, initial weights, AdamW,
+            and seed rows encoded as genes.
 
 Parity status (see each module's header): the forward model and the EA operators are
 pinned by tests under ``tests/`` that do not re-type the oracle's formulas; whole EA runs
