@@ -16,6 +16,8 @@
 #include <tuple>
 #include <vector>
 
+#include "../../include/sblm_cnn.h"
+#include "cnn_launch.cuh"
 #include "ea_launch.cuh"
 #include "forward_run.cuh"
 #include "runtime.cuh"
@@ -49,6 +51,8 @@ struct BatchArgs {
     double* best_theta;
     double* best_chi2;
     int max_ep;        // longest lightcurve the staging area holds
+    const double* seed;  // [n_lc][n_seed][6] genes of the seeded rows, or null
+    int n_seed;          // rows n_pop - n_seed .. n_pop - 1 of the first population
 };
 
 size_t batch_smem_bytes(int mode, int n_pop, int n2, int max_ep) {
@@ -93,6 +97,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
         for (int e = threadIdx.x; e < m; e += blockDim.x) keys[e] = init_key(c, 0, (uint64_t)e);
         __syncthreads();
         block_init_values(c, 0, keys, m, Pb[0], 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key), a.n2);
+        if (a.n_seed > 0) {  // proposal rows replace the last n_seed random rows
+            __syncthreads();
+            const double* sg = a.seed + (size_t)lc * a.n_seed * n_par;
+            double* dst = Pb[0] + (size_t)(n_pop - a.n_seed) * n_par;
+            for (int e = threadIdx.x; e < a.n_seed * n_par; e += blockDim.x) dst[e] = sg[e];
+        }
         if (threadIdx.x == 0) state_reset(c, s_state);
         __syncthreads();
 
@@ -206,7 +216,8 @@ struct Prepared {
 // validate, stage and lay out one batch call; on success `st` has begun
 sblm_status prepare(const double* t, const double* flux, const double* sigma, const int64_t* offsets, int32_t n_lc,
                     const sblm_bounds* bounds, const sblm_ea_params* params, const sblm_batch_tuning* tuning,
-                    double* best_theta, double* best_chi2, Staging& st, int* i_th, int* i_c, Prepared* out) {
+                    const double* seed_genes, int n_seed, double* best_theta, double* best_chi2, Staging& st,
+                    int* i_th, int* i_c, Prepared* out, size_t extra_bytes = 0, int* k_extra = nullptr) {
     EAConst c;
     SBLM_TRY(ea_const(params, params ? params->n_pop : 0, SBLM_NPAR, 0, &c));
     if (params->n_gen < 1) return fail(SBLM_EINVAL, "n_gen must be >= 1");
@@ -266,6 +277,11 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     const int k_keys = st.scratch(sizeof(uint64_t) * (size_t)c.n_pop * SBLM_NPAR * blocks);
     const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
     const int k_next = st.scratch(sizeof(unsigned));
+    if (n_seed < 0 || n_seed > c.n_pop) return fail(SBLM_EINVAL, "n_seed must be in [0, n_pop]");
+    if (n_seed > 0 && !seed_genes && !k_extra) return fail(SBLM_EINVAL, "seed_genes is NULL");
+    int i_seed = -1;
+    if (seed_genes) SBLM_TRY(st.arg(seed_genes, sizeof(double) * SBLM_NPAR * (size_t)n_lc * n_seed, true, false, &i_seed));
+    if (k_extra) *k_extra = st.scratch(extra_bytes);
     SBLM_TRY(st.begin());
     // longest first (stable): the classic longest-processing-time order for the work queue
     std::vector<int> order(n_lc);
@@ -294,6 +310,8 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.best_theta = static_cast<double*>(st.dev(*i_th));
     a.best_chi2 = static_cast<double*>(st.dev(*i_c));
     a.max_ep = max_ep;
+    a.seed = i_seed >= 0 ? static_cast<const double*>(st.dev(i_seed)) : nullptr;
+    a.n_seed = n_seed;
     out->a = a;
     out->blocks = blocks;
     out->threads = threads;
@@ -353,16 +371,55 @@ sblm_status run_graph(const Prepared& p, cudaStream_t s) {
 
 using namespace sblm;
 
-extern "C" sblm_status sblm_fit_batch_tuned(const double* t, const double* flux, const double* sigma,
-                                            const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
-                                            const sblm_ea_params* params, const sblm_batch_tuning* tuning,
-                                            double* best_theta, double* best_chi2, void* stream) {
+extern "C" sblm_status sblm_fit_batch_seeded(const double* t, const double* flux, const double* sigma,
+                                             const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                             const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                             const double* seed_genes, int32_t n_seed, double* best_theta,
+                                             double* best_chi2, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CallLock lock;
     Staging st(s);
     int i_th, i_c;
     Prepared p;
-    SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, best_theta, best_chi2, st, &i_th, &i_c, &p));
+    SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, n_seed > 0 ? seed_genes : nullptr, n_seed,
+                     best_theta, best_chi2, st, &i_th, &i_c, &p));
+    SBLM_TRY(run_graph(p, s));
+    SBLM_TRY(st.end());
+    SBLM_CUDA(cudaStreamSynchronize(s));
+    return SBLM_OK;
+}
+
+extern "C" sblm_status sblm_fit_batch_tuned(const double* t, const double* flux, const double* sigma,
+                                            const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                            const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                            double* best_theta, double* best_chi2, void* stream) {
+    return sblm_fit_batch_seeded(t, flux, sigma, offsets, n_lc, bounds, params, tuning, nullptr, 0, best_theta,
+                                 best_chi2, stream);
+}
+
+extern "C" sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, const double* sigma,
+                                          const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                          const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                          const float* weights, double seed_frac, double* best_theta,
+                                          double* best_chi2, void* stream) {
+    if (!(seed_frac >= 0.0 && seed_frac <= 1.0)) return fail(SBLM_EINVAL, "seed_frac must be in [0, 1]");
+    if (!params) return fail(SBLM_EINVAL, "params is NULL");
+    const int n_seed = weights ? (int)std::lround(seed_frac * params->n_pop) : 0;
+    if (n_seed == 0)
+        return sblm_fit_batch_seeded(t, flux, sigma, offsets, n_lc, bounds, params, tuning, nullptr, 0, best_theta,
+                                     best_chi2, stream);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    int i_th, i_c, k_inf = -1, i_w = -1;
+    SBLM_TRY(st.arg(weights, sizeof(float) * cnn::kNParams, true, false, &i_w));
+    Prepared p;
+    SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, nullptr, n_seed, best_theta, best_chi2, st,
+                     &i_th, &i_c, &p, cnn::infer_scratch_bytes(n_lc, n_seed), &k_inf));
+    const cnn::InferScratch sc = cnn::infer_scratch_carve(st.scratch_ptr(k_inf), n_lc, n_seed);
+    SBLM_CUDA(cnn::launch_seed_rows(p.a.t, p.a.flux, p.a.sigma, p.a.offsets, n_lc,
+                                    static_cast<const float*>(st.dev(i_w)), p.a.b, n_seed, params->seed, sc, s));
+    p.a.seed = sc.genes;
     SBLM_TRY(run_graph(p, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));

@@ -1,4 +1,4 @@
-"""Python binding of ``libsblm.so`` (the C ABI declared in include/sblm.h).
+"""Python binding of ``libsblm.so`` (the C ABI declared in include/sblm.h and include/sblm_cnn.h).
 
 Argument marshalling only: every step of the computation runs in the library's CUDA kernels.
 Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CUDA tensors are passed as device
@@ -66,6 +66,22 @@ class BatchTuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("block", ctypes.c_int32)]
 
 
+class CnnTrainParams(ctypes.Structure):
+    _fields_ = [
+        ("batch", ctypes.c_int32),
+        ("n_steps", ctypes.c_int32),
+        ("warmup", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("lr", ctypes.c_double),
+        ("beta1", ctypes.c_double),
+        ("beta2", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("weight_decay", ctypes.c_double),
+        ("forced_frac", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
 _p = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _u64 = ctypes.c_uint64
@@ -94,6 +110,26 @@ _SIGS = {
         ctypes.c_int,
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p],
     ),
+    "sblm_fit_batch_seeded": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p,
+         _i32, _p, _p, _p],
+    ),
+    "sblm_fit_batch_cnn": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p,
+         ctypes.c_double, _p, _p, _p],
+    ),
+    "sblm_cnn_train_params_default": (None, [ctypes.POINTER(CnnTrainParams)]),
+    "sblm_cnn_num_params": (ctypes.c_int32, []),
+    "sblm_cnn_init": (ctypes.c_int, [_p, _u64, _p]),
+    "sblm_cnn_make_batch": (ctypes.c_int, [_u64, ctypes.c_int64, _i32, ctypes.c_double, _i32, _p, _p, _p, _p]),
+    "sblm_cnn_bin": (ctypes.c_int, [_p, _p, _p, _p, _i32, _p, _p, _p]),
+    "sblm_cnn_forward": (ctypes.c_int, [_p, _p, _i32, _p, _p]),
+    "sblm_cnn_loss_grad": (ctypes.c_int, [_p, _p, _p, _i32, _p, _p, _p]),
+    "sblm_cnn_adamw": (ctypes.c_int, [_p, _p, _p, ctypes.POINTER(CnnTrainParams), ctypes.c_int64, _p]),
+    "sblm_cnn_train": (ctypes.c_int, [_p, _p, ctypes.POINTER(CnnTrainParams), ctypes.c_int64, _i32, _p, _p]),
+    "sblm_cnn_propose": (ctypes.c_int, [_p, _p, _i32, ctypes.POINTER(Bounds), _i32, _u64, _p, _p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -155,7 +191,7 @@ def _like(ref, shape, dtype):
         import torch
 
         if isinstance(ref, torch.Tensor):
-            tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+            tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
             return torch.empty(shape, dtype=tdt, device=ref.device)
     except ImportError:
         pass
@@ -293,10 +329,32 @@ def fit(t, flux, sigma, lo, hi, p, trace=False, stream=None):
     return (best, float(best_chi2[0]), tr) if trace else (best, float(best_chi2[0]))
 
 
-def fit_batch(t, flux, sigma, offsets, lo, hi, p, tuning=None, stream=None):
+def _tuning(tuning, t, flux, sigma, offsets, lo, hi, p, stream):
+    if isinstance(tuning, str) and tuning == "auto":
+        tuning = autotune_batch(t, flux, sigma, offsets, lo, hi, p, stream=stream)
+    if isinstance(tuning, tuple):
+        tuning = BatchTuning(*tuning)
+    return tuning
+
+
+def fit_batch(t, flux, sigma, offsets, lo, hi, p, tuning=None, seed_genes=None, stream=None):
     """Best theta [n_lc, 6] and chi^2 [n_lc] of lightcurves concatenated at ``offsets`` [n_lc + 1]
     (int64). ``tuning``: a BatchTuning, a (group, block) pair, "auto" (the cached autotuner result
-    for this workload's shape, tuned on first use) or None (the library's defaults)."""
+    for this workload's shape, tuned on first use) or None (the library's defaults).
+    ``seed_genes`` [n_lc, n_seed, 6]: rows that replace the last n_seed rows of each first population."""
+    if seed_genes is not None:
+        n_lc = int(offsets.shape[0]) - 1
+        b = bounds(lo, hi)
+        best = np.empty((n_lc, 6))
+        best_chi2 = np.empty(n_lc)
+        tuning = _tuning(tuning, t, flux, sigma, offsets, lo, hi, p, stream)
+        a = [_ptr(x) for x in (t, flux, sigma, offsets, seed_genes)]
+        s = _stream(stream, t, flux, sigma, seed_genes)
+        tp = ctypes.byref(tuning) if tuning is not None else None
+        st = _lib.sblm_fit_batch_seeded(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p), tp,
+                                        a[4][0], int(seed_genes.shape[1]), best.ctypes.data, best_chi2.ctypes.data, s)
+        _check(st, "sblm_fit_batch_seeded")
+        return best, best_chi2
     n_lc = int(offsets.shape[0]) - 1
     b = bounds(lo, hi)
     best = np.empty((n_lc, 6))
@@ -358,6 +416,138 @@ def autotune_batch(t, flux, sigma, offsets, lo, hi, p, trial_generations=2, stre
         except OSError:
             pass
     return best
+
+
+def fit_batch_cnn(t, flux, sigma, offsets, lo, hi, p, weights, seed_frac=0.5, tuning=None, stream=None):
+    """The proposal-seeded batched fit: the network's seed rows replace round(seed_frac * n_pop)
+    rows of each first population (weights None: the paper's fitter)."""
+    n_lc = int(offsets.shape[0]) - 1
+    b = bounds(lo, hi)
+    best = np.empty((n_lc, 6))
+    best_chi2 = np.empty(n_lc)
+    tuning = _tuning(tuning, t, flux, sigma, offsets, lo, hi, p, stream)
+    a = [_ptr(x) for x in (t, flux, sigma, offsets, weights)]
+    s = _stream(stream, t, flux, sigma, weights)
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    st = _lib.sblm_fit_batch_cnn(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p), tp,
+                                 a[4][0], float(seed_frac), best.ctypes.data, best_chi2.ctypes.data, s)
+    _check(st, "sblm_fit_batch_cnn")
+    return best, best_chi2
+
+
+# ------------------------------------------------------------------------------------------
+# learned proposal (include/sblm_cnn.h)
+# ------------------------------------------------------------------------------------------
+CNN_BINS = 256
+
+
+def cnn_num_params():
+    return int(_lib.sblm_cnn_num_params())
+
+
+def cnn_train_params(**kw):
+    """A CnnTrainParams with the library's defaults, then ``kw``."""
+    p = CnnTrainParams()
+    _lib.sblm_cnn_train_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "precision":
+            v = _precision(v)
+        setattr(p, k, v)
+    return p
+
+
+def _empty(device, shape, dtype):
+    if device is None:
+        return np.empty(shape, dtype=dtype)
+    import torch
+
+    tdt = {np.float64: torch.float64, np.float32: torch.float32}[dtype]
+    return torch.empty(shape, dtype=tdt, device=device)
+
+
+def cnn_init(seed=0, device="cuda", stream=None):
+    """Initial FP32 weights [N] on ``device`` (None: host numpy)."""
+    w = _empty(device, (cnn_num_params(),), np.float32)
+    pw, _a = _ptr(w)
+    _check(_lib.sblm_cnn_init(pw, seed, _stream(stream, w)), "sblm_cnn_init")
+    return w
+
+
+def cnn_make_batch(seed, step, batch, forced_frac=0.1, precision="mixed", device="cuda", stream=None):
+    """Training batch drawn at optimiser step ``step``: x [B, 256, 2], y [B, 6], theta [B, 6]."""
+    x = _empty(device, (batch, CNN_BINS, 2), np.float32)
+    y = _empty(device, (batch, 6), np.float32)
+    th = _empty(device, (batch, 6), np.float64)
+    px, _a = _ptr(x)
+    py, _b = _ptr(y)
+    pt, _c = _ptr(th)
+    st = _lib.sblm_cnn_make_batch(seed, step, batch, float(forced_frac), _precision(precision), px, py, pt,
+                                  _stream(stream, x))
+    _check(st, "sblm_cnn_make_batch")
+    return x, y, th
+
+
+def cnn_bin(t, flux, sigma, offsets, stream=None):
+    """Network inputs x [n_lc, 256, 2] and windows (c, h) [n_lc, 2] of concatenated lightcurves."""
+    n_lc = int(offsets.shape[0]) - 1
+    x = _like(t, (n_lc, CNN_BINS, 2), np.float32)
+    w = _like(t, (n_lc, 2), np.float64)
+    a = [_ptr(v) for v in (t, flux, sigma, offsets, x, w)]
+    st = _lib.sblm_cnn_bin(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, a[4][0], a[5][0], _stream(stream, t, x))
+    _check(st, "sblm_cnn_bin")
+    return x, w
+
+
+def cnn_forward(weights, x, stream=None):
+    """Network outputs [B, 12]: 6 means then 6 log-variances."""
+    B = int(x.shape[0])
+    out = _like(x, (B, 12), np.float32)
+    a = [_ptr(v) for v in (weights, x, out)]
+    _check(_lib.sblm_cnn_forward(a[0][0], a[1][0], B, a[2][0], _stream(stream, weights, x)), "sblm_cnn_forward")
+    return out
+
+
+def cnn_loss_grad(weights, x, y, stream=None):
+    """(loss, gradient [N]) of the Gaussian NLL for the batch (x, y)."""
+    B = int(x.shape[0])
+    g = _like(weights, (cnn_num_params(),), np.float32)
+    loss = np.empty(1)
+    a = [_ptr(v) for v in (weights, x, y, g)]
+    st = _lib.sblm_cnn_loss_grad(a[0][0], a[1][0], a[2][0], B, loss.ctypes.data, a[3][0],
+                                 _stream(stream, weights, x))
+    _check(st, "sblm_cnn_loss_grad")
+    return float(loss[0]), g
+
+
+def cnn_adamw(weights, state, grad, p, t, stream=None):
+    """One AdamW step in place (state [2 N]: first then second moments)."""
+    a = [_ptr(v) for v in (weights, state, grad)]
+    st = _lib.sblm_cnn_adamw(a[0][0], a[1][0], a[2][0], ctypes.byref(p), int(t), _stream(stream, weights))
+    _check(st, "sblm_cnn_adamw")
+
+
+def cnn_train(weights, state, p, first_step=0, n_run=None, stream=None):
+    """Steps first_step .. first_step + n_run - 1 of the schedule on the device; returns the
+    per-step batch losses (numpy)."""
+    n_run = p.n_steps - first_step if n_run is None else n_run
+    hist = np.empty(max(0, n_run), dtype=np.float32)
+    a = [_ptr(v) for v in (weights, state)]
+    st = _lib.sblm_cnn_train(a[0][0], a[1][0], ctypes.byref(p), int(first_step), int(n_run), hist.ctypes.data,
+                             _stream(stream, weights))
+    _check(st, "sblm_cnn_train")
+    return hist
+
+
+def cnn_propose(out, window, lo, hi, n_seed, seed, stream=None):
+    """Seed rows [n_lc, n_seed, 6] (genes) drawn from the network outputs."""
+    n_lc = int(out.shape[0])
+    b = bounds(lo, hi)
+    g = _like(window, (n_lc, n_seed, 6), np.float64)
+    a = [_ptr(v) for v in (out, window, g)]
+    st = _lib.sblm_cnn_propose(a[0][0], a[1][0], n_lc, ctypes.byref(b), n_seed, seed, a[2][0],
+                               _stream(stream, out, window))
+    _check(st, "sblm_cnn_propose")
+    return g
 
 
 def peak_rates(stream=None):

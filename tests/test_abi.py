@@ -1,5 +1,5 @@
 """The C-ABI library loads on a machine without a GPU, exports every entry point that
-include/sblm.h declares, and its structs have the layout the binding assumes. Only calls that
+include/*.h declares, and its structs have the layout the binding assumes. Only calls that
 fail argument validation before touching CUDA are made here."""
 import ctypes
 import os
@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "sblm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include"))) if h.endswith(".h")]
 LIB = os.path.join(ROOT, "paper_1208_4830_gb300", "libsblm.so")
 
 
@@ -27,7 +27,7 @@ def built():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(sblm_[a-z0-9_]+)\s*\(", text)))
 
@@ -107,3 +107,40 @@ def test_binding_refuses_to_run_without_library(tmp_path):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_cnn_abi_layout_and_validation(built, tmp_path):
+    from oracle import cnn as ocnn
+
+    lib = built._lib
+    assert built.cnn_num_params() == ocnn.N_PARAMS
+    gcc = shutil.which("gcc")
+    if gcc:
+        src = tmp_path / "cnn_layout.c"
+        src.write_text(
+            '#include <stdio.h>\n#include <stddef.h>\n#include "sblm_cnn.h"\n'
+            'int main(void){printf("%zu %zu %zu\\n", sizeof(sblm_cnn_train_params),'
+            " offsetof(sblm_cnn_train_params, lr), offsetof(sblm_cnn_train_params, seed)); return 0;}\n"
+        )
+        exe = tmp_path / "cnn_layout"
+        subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+        got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+        T = built.CnnTrainParams
+        assert got == [ctypes.sizeof(T), T.lr.offset, T.seed.offset]
+    p = built.cnn_train_params()
+    assert (p.batch, p.n_steps, p.precision, p.lr, p.forced_frac) == (256, 4096, 1, 2e-3, 0.1)
+    # rejected before any CUDA call
+    assert lib.sblm_cnn_make_batch(0, 0, 0, 0.1, 1, None, None, None, None) == 1
+    assert lib.sblm_cnn_make_batch(0, 0, 4, 1.5, 1, None, None, None, None) == 1
+    assert lib.sblm_cnn_forward(None, None, 0, None, None) == 1
+    assert lib.sblm_cnn_loss_grad(None, None, None, 4, None, None, None) == 1
+    bad = built.cnn_train_params(batch=0)
+    assert lib.sblm_cnn_train(None, None, ctypes.byref(bad), 0, 1, None, None) == 1
+    bad = built.cnn_train_params(lr=-1.0)
+    assert lib.sblm_cnn_adamw(None, None, None, ctypes.byref(bad), 1, None) == 1
+    b = built.bounds([0, 5, 0, 0, 0.3, -4], [0, 100, 1, 6, 3, 0])
+    assert lib.sblm_cnn_propose(None, None, 1, ctypes.byref(b), 4, 0, None, None) == 1
+    assert lib.sblm_cnn_bin(None, None, None, None, 0, None, None, None) == 1
+    pp = built.params(n_pop=64)
+    assert lib.sblm_fit_batch_cnn(None, None, None, None, 1, None, ctypes.byref(pp), None, None, 2.0, None, None,
+                                  None) == 1

@@ -1,0 +1,212 @@
+"""The learned proposal on the device against its oracle (oracle/cnn.py, oracle/proposal.py):
+initial weights, network outputs and gradients (BF16 tensor-core kernels against FP64), AdamW,
+the training-curve generator, binning of observed curves, seed sampling, the seeded batched fit,
+and training on the device."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn as ocnn
+from oracle import proposal as op
+from oracle import sblm as osb
+from paper_1208_4830_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# BF16 operands (8-bit mantissa) with FP32 accumulation against FP64: normwise relative error of a
+# tensor of products, and the cosine between gradient tensors
+BF16_REL = 3e-2
+COS_MIN = 0.999
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _cos(a, b):
+    return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def _weights(seed, bias_scale=0.1):
+    """Oracle initial weights with non-zero biases, so every term of the gradient is exercised."""
+    w = op.init_params(seed)
+    g = np.random.default_rng(seed + 100)
+    p = ocnn.unflatten(w)
+    for name, shape in ocnn.SHAPES:
+        if name.startswith("b"):
+            p[name] = g.normal(0.0, bias_scale, shape)
+    return ocnn.flatten(p)
+
+
+def _inputs(seed, B):
+    g = np.random.default_rng(seed)
+    x = np.zeros((B, 256, 2))
+    x[:, :, 1] = g.uniform(size=(B, 256)) > 0.15
+    x[:, :, 0] = np.where(x[:, :, 1] > 0, g.normal(0, 0.7, (B, 256)), 0.0)
+    y = np.stack([g.uniform(-0.4, 0.4, B), g.uniform(-3, 0.4, B), g.uniform(0, 1, B), g.uniform(0, 1, B),
+                  g.uniform(-1.2, 1.1, B), g.uniform(-4, 0, B)], axis=1)
+    return x, y
+
+
+def test_init_matches_oracle(lib):
+    w = lib.cnn_init(seed=3).cpu().numpy()
+    np.testing.assert_allclose(w, op.init_params(3), rtol=2e-7, atol=1e-30)
+
+
+@pytest.mark.parametrize("B", [1, 5, 37])
+def test_forward_matches_oracle(lib, B):
+    w = _weights(1)
+    x, _ = _inputs(2 + B, B)
+    out = lib.cnn_forward(torch.tensor(w, dtype=torch.float32, device="cuda"),
+                          torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ref, _ = ocnn.forward(w, x)
+    assert _rel(out, ref) <= BF16_REL, _rel(out, ref)
+
+
+@pytest.mark.parametrize("B", [3, 64, 130])
+def test_gradients_match_oracle(lib, B):
+    w = _weights(4)
+    x, y = _inputs(5 + B, B)
+    wt = torch.tensor(w, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    loss, g = lib.cnn_loss_grad(wt, xt, yt)
+    g = g.cpu().numpy().astype(np.float64)
+    ref_loss, ref_g = ocnn.loss_and_grad(w, x, y)
+    assert loss == pytest.approx(ref_loss, rel=BF16_REL)
+    o = 0
+    for name, shape in ocnn.SHAPES:
+        n = int(np.prod(shape))
+        a, b = g[o : o + n], ref_g[o : o + n]
+        assert _rel(a, b) <= BF16_REL, (name, _rel(a, b))
+        assert _cos(a, b) >= COS_MIN, (name, _cos(a, b))
+        o += n
+    # the reduction order is fixed: a second call is bit-identical
+    loss2, g2 = lib.cnn_loss_grad(wt, xt, yt)
+    assert loss2 == loss and np.array_equal(g2.cpu().numpy(), g.astype(np.float32))
+
+
+def test_adamw_matches_oracle(lib):
+    N = ocnn.N_PARAMS
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=N).astype(np.float32)
+    m = (0.01 * rng.normal(size=N)).astype(np.float32)
+    v = (1e-4 * rng.uniform(size=N)).astype(np.float32)
+    grad = rng.normal(size=N).astype(np.float32)
+    p = lib.cnn_train_params(lr=3e-3, n_steps=100, warmup=10)
+    wt = torch.tensor(w, device="cuda")
+    st = torch.tensor(np.concatenate([m, v]), device="cuda")
+    lib.cnn_adamw(wt, st, torch.tensor(grad, device="cuda"), p, 7)
+    lr = op.lr_at(7, 100, 10, 3e-3)
+    w2, m2, v2 = op.adamw(w.astype(np.float64), m.astype(np.float64), v.astype(np.float64), grad.astype(np.float64),
+                          7, lr, 0.9, 0.999, 1e-8, 1e-4)
+    np.testing.assert_allclose(wt.cpu().numpy(), w2, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(st[:N].cpu().numpy(), m2, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(st[N:].cpu().numpy(), v2, rtol=1e-6, atol=1e-15)
+
+
+@pytest.mark.parametrize("forced", [0.0, 0.5])
+def test_make_batch_matches_oracle_fp64(lib, forced):
+    B = 24
+    x, y, th = lib.cnn_make_batch(seed=9, step=3, batch=B, forced_frac=forced, precision="fp64")
+    X, Y, TH, infos = op.make_batch(9, 3, B, forced)
+    np.testing.assert_allclose(th.cpu().numpy(), TH, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(y.cpu().numpy(), Y, rtol=2e-6, atol=1e-6)
+    xd = x.cpu().numpy()
+    assert np.array_equal(xd[:, :, 1], X[:, :, 1])  # mask decisions are taken in FP64 on both sides
+    np.testing.assert_allclose(xd[:, :, 0], X[:, :, 0], atol=1e-5)
+    if forced:
+        assert sum(i["forced"] for i in infos) >= 5
+
+
+def test_make_batch_mixed_generator(lib):
+    B = 64
+    x, _, th = lib.cnn_make_batch(seed=2, step=11, batch=B, forced_frac=0.1, precision="mixed")
+    X, _, TH, _ = op.make_batch(2, 11, B, 0.1)
+    xd = x.cpu().numpy()
+    assert np.array_equal(xd[:, :, 1], X[:, :, 1])
+    err = np.abs(xd[:, :, 0] - X[:, :, 0])
+    assert np.quantile(err, 0.995) <= 1e-3 and np.all(np.isfinite(xd))
+
+
+def test_bin_matches_oracle(lib):
+    b = synth.seasonal_batch(6, seed=12, n_min=100, n_max=2500, span=(-100.0, 100.0), season=80.0, gap=30.0)
+    A = np.concatenate([osb.magnification(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]])[0]
+                        for i in range(6)])
+    flux, sigma = b.observe(A)
+    x, win = lib.cnn_bin(torch.tensor(b.t, device="cuda"), torch.tensor(flux, device="cuda"),
+                         torch.tensor(sigma, device="cuda"), torch.tensor(b.offsets, device="cuda"))
+    x, win = x.cpu().numpy(), win.cpu().numpy()
+    for i in range(6):
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        X, (c, h) = op.bin_lightcurve(b.t[sl], flux[sl], sigma[sl])
+        assert win[i, 0] == pytest.approx(c, rel=1e-15, abs=1e-13) and win[i, 1] == pytest.approx(h, rel=1e-15)
+        assert np.array_equal(x[i, :, 1], X[:, 1])
+        np.testing.assert_allclose(x[i, :, 0], X[:, 0], atol=1e-6)
+    # host buffers give the same inputs
+    xh, _ = lib.cnn_bin(b.t, flux, sigma, b.offsets)
+    assert np.array_equal(xh, x)
+
+
+def test_propose_matches_oracle(lib):
+    rng = np.random.default_rng(3)
+    n_lc, n_seed = 5, 33
+    out = np.concatenate([rng.normal(0, 0.5, (n_lc, 6)), rng.normal(-2, 1, (n_lc, 6))], axis=1).astype(np.float32)
+    out[2, 1] = 30.0  # far outside the tE bounds: clamped
+    win = np.stack([rng.uniform(-10, 10, n_lc), rng.uniform(40, 120, n_lc)], axis=1)
+    g = lib.cnn_propose(torch.tensor(out, device="cuda"), torch.tensor(win, device="cuda"), synth.FIT_LO, synth.FIT_HI,
+                        n_seed, seed=5).cpu().numpy()
+    ref = op.propose_genes(out, win, synth.FIT_LO, synth.FIT_HI, n_seed, 5)
+    np.testing.assert_allclose(g, ref, rtol=1e-12, atol=1e-12)
+    assert g.min() >= 0 and g.max() <= 1 and np.all(g[2, :, 1] == 1.0)
+
+
+def _batch(n_lc, seed, n_min, n_max):
+    b = synth.seasonal_batch(n_lc, seed=seed, n_min=n_min, n_max=n_max, span=(-100.0, 100.0), season=80.0, gap=30.0)
+    A = np.concatenate([osb.magnification(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]])[0]
+                        for i in range(n_lc)])
+    flux, sigma = b.observe(A)
+    return b, flux, sigma
+
+
+def _genes(theta):
+    v = theta.copy()
+    v[..., 5] = np.log10(v[..., 5])
+    return (v - synth.FIT_LO) / (synth.FIT_HI - synth.FIT_LO)
+
+
+def test_seeded_rows_enter_the_first_population(lib):
+    """With the encoded truth among the seed rows and a single generation, the best chi^2 found
+    is at most the truth's (the first generation evaluates every seeded row)."""
+    b, flux, sigma = _batch(4, seed=21, n_min=150, n_max=300)
+    p = lib.params(n_pop=64, n_gen=1, precision="fp64", seed=1)
+    seeds = np.repeat(_genes(b.truth)[:, None, :], 3, axis=1)
+    seeds[:, 1:] = np.clip(seeds[:, 1:] + 0.05, 0, 1)
+    _, chi = lib.fit_batch(b.t, flux, sigma, b.offsets, synth.FIT_LO, synth.FIT_HI, p, seed_genes=seeds)
+    _, chi_plain = lib.fit_batch(b.t, flux, sigma, b.offsets, synth.FIT_LO, synth.FIT_HI, p)
+    for i in range(4):
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        c_true = osb.chi2(b.truth[i : i + 1], b.t[sl], flux[sl], sigma[sl])[0]
+        assert chi[i] <= c_true * (1 + 1e-9) + 1e-9, (i, chi[i], c_true)
+        assert chi_plain[i] > c_true  # one random generation does not find the truth
+    # n_seed = 0 and no seeds: the paper's fitter, identical to sblm_fit_batch
+    best0, chi0 = lib.fit_batch(b.t, flux, sigma, b.offsets, synth.FIT_LO, synth.FIT_HI, p,
+                                seed_genes=np.zeros((4, 0, 6)))
+    np.testing.assert_array_equal(chi0, chi_plain)
+
+
+def test_training_on_device_reduces_the_loss(lib):
+    w = lib.cnn_init(seed=0)
+    st = torch.zeros(2 * lib.cnn_num_params(), device="cuda")
+    p = lib.cnn_train_params(batch=128, n_steps=400, warmup=40, seed=4)
+    hist = lib.cnn_train(w, st, p)
+    assert hist.shape == (400,) and np.all(np.isfinite(hist))
+    assert hist[-50:].mean() < hist[:20].mean() - 1.0, (hist[:20].mean(), hist[-50:].mean())
+    # resuming continues the same schedule and data stream
+    w2 = lib.cnn_init(seed=0)
+    st2 = torch.zeros_like(st)
+    h1 = lib.cnn_train(w2, st2, p, first_step=0, n_run=150)
+    h2 = lib.cnn_train(w2, st2, p, first_step=150, n_run=250)
+    np.testing.assert_allclose(np.concatenate([h1, h2]), hist, rtol=1e-5, atol=1e-5)
