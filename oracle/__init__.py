@@ -17,6 +17,7 @@ Modules
             paper's order, plus a reference driver.
 ``cnn``     the learned proposal network (not in the paper: this project's seeding of the
             initial population), forward and backward by hand in FP64.
+``polish``  the amoeba (downhill simplex) fine-tuning of the fittest solution, Section 4.1.
 ``proposal`` the proposal's data path: training curves, binning, initial weights, AdamW,
             and seed rows encoded as genes.
 
