@@ -75,7 +75,10 @@ typedef struct {
     double stag_rel;       /* stagnant if the best improved by <= stag_rel over the window (0.01) */
     int32_t restart_after; /* consecutive stagnant generations before a restart (10) */
     int32_t precision;     /* SBLM_FP64, SBLM_MIXED or SBLM_FP32 for the fitness evaluation */
-    int32_t reserved;      /* must be 0 */
+    int32_t polish_fev;    /* amoeba fine-tuning of the fittest solution after the EA (Section 4.1,
+                              "EA with amoeba"): at most this many chi^2 evaluations of a
+                              downhill-simplex search in the genes (sblm_fit, sblm_fit_batch*);
+                              0 = the EA alone (default) */
     uint64_t seed;         /* Philox4x64-10 key word 0; key word 1 is the population's stream id */
 } sblm_ea_params;
 
@@ -253,6 +256,23 @@ sblm_status sblm_autotune_batch(const double* t, const double* flux, const doubl
                                 const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
                                 const sblm_ea_params* params, int32_t trial_generations,
                                 sblm_batch_tuning* best, double* best_ms, void* stream);
+
+/*
+ * Amoeba fine-tuning (Section 4.1: the EA "with amoeba"; Nelder & Mead 1965 with the standard
+ * coefficients of Lagarias et al. 1998) of given solutions: for each lightcurve (layout of
+ * sblm_fit_batch), a downhill-simplex search in the genes over `bounds` starting from
+ * genes_in[l] (6 genes in [0, 1]): start simplex x0 + 0.03 e_j (-0.03 where that leaves [0, 1]),
+ * reflection 1, expansion 2, contraction 1/2, shrink 1/2, trial points clamped to [0, 1], the
+ * simplex rebuilt around its best vertex whenever it has collapsed to 1e-9, stopped after
+ * `maxfev` chi^2 evaluations (a step in progress may take up to 6 more). The chi^2 is that of
+ * sblm_chi2_genes in `precision`. genes_out [n_lc * 6] (may alias genes_in) receives the best
+ * vertex, chi2_out [n_lc] its chi^2. The longest lightcurve must fit 200 KB of shared memory
+ * (24 bytes per epoch in FP64, 16 otherwise). 0 <= maxfev <= 2^20.
+ */
+sblm_status sblm_polish_batch(const double* t, const double* flux, const double* sigma,
+                              const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                              const double* genes_in, int32_t maxfev, int32_t precision,
+                              double* genes_out, double* chi2_out, void* stream);
 
 /*
  * Measured FMA throughput of the current device, in TFLOP/s (an FMA counts as 2 flop): eight

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsblm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
-SOURCES = ["runtime.cu", "forward.cu", "ea.cu", "fit.cu", "batch.cu", "peaks.cu", "cnn.cu"]
+SOURCES = ["runtime.cu", "forward.cu", "ea.cu", "fit.cu", "batch.cu", "peaks.cu", "cnn.cu", "polish.cu"]
 
 
 def nvcc():

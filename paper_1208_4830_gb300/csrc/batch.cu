@@ -20,6 +20,7 @@
 #include "cnn_launch.cuh"
 #include "ea_launch.cuh"
 #include "forward_run.cuh"
+#include "polish_launch.cuh"
 #include "runtime.cuh"
 
 namespace sblm {
@@ -53,6 +54,8 @@ struct BatchArgs {
     int max_ep;        // longest lightcurve the staging area holds
     const double* seed;  // [n_lc][n_seed][6] genes of the seeded rows, or null
     int n_seed;          // rows n_pop - n_seed .. n_pop - 1 of the first population
+    int polish_fev;      // amoeba fine-tuning of the archive's best (0: none), a separate launch
+    double* best_genes;  // [n_lc][6] genes of best_chi2
 };
 
 size_t batch_smem_bytes(int mode, int n_pop, int n2, int max_ep) {
@@ -174,9 +177,21 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
             for (int j = 0; j < 5; ++j) th[j] = av[j];
             th[5] = exp10(av[5]);
             a.best_chi2[lc] = s_state.best_chi2;
+            for (int j = 0; j < SBLM_NPAR; ++j) a.best_genes[(size_t)lc * SBLM_NPAR + j] = s_state.best_genes[j];
         }
         __syncthreads();
     }
+}
+
+// theta rows of the (polished) best genes
+__global__ void genes_to_theta_kernel(const double* __restrict__ genes, int n_lc, Bounds b, double* __restrict__ theta) {
+    const int lc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lc >= n_lc) return;
+    double av[SBLM_NPAR];
+    for (int j = 0; j < SBLM_NPAR; ++j) av[j] = b.lo[j] + (b.hi[j] - b.lo[j]) * genes[(size_t)lc * SBLM_NPAR + j];
+    double* th = theta + (size_t)lc * SBLM_NPAR;
+    for (int j = 0; j < 5; ++j) th[j] = av[j];
+    th[5] = exp10(av[5]);
 }
 
 template <int MODE>
@@ -211,6 +226,9 @@ struct Prepared {
     int blocks, threads;
     size_t smem;
     int mode;
+    PolishArgs pa;   // amoeba pass over every lightcurve when a.polish_fev > 0
+    int polish_blocks;
+    int max_ep;
 };
 
 // validate, stage and lay out one batch call; on success `st` has begun
@@ -270,14 +288,26 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     SBLM_TRY(is_device_pointer(flux, &d2));
     SBLM_TRY(is_device_pointer(sigma, &d3));
     if (!d1 && !d2 && !d3) SBLM_TRY(check_lightcurve_host(t, flux, sigma, (int)total));
-    // per block: epochs past this are re-solved in place (a speed choice only)
-    const unsigned qcap = mode == SBLM_MIXED ? std::min(mixed_queue_capacity(c.n_pop, max_ep), 32768u) : 0;
+    // per block: room for a quarter of a generation's epochs (a population gathered on a
+    // caustic-crossing model defers many); epochs past this are re-solved in place, one divergent
+    // lane at a time, so the size is a speed choice only
+    const unsigned qcap =
+        mode == SBLM_MIXED ? (unsigned)std::min<long>(std::max<long>((long)c.n_pop * max_ep / 4, 4096), 65536) : 0;
     const int k_order = st.scratch(sizeof(int) * n_lc);
     const int k_P = st.scratch(sizeof(double) * 2 * (size_t)c.n_pop * SBLM_NPAR * blocks);
     const int k_keys = st.scratch(sizeof(uint64_t) * (size_t)c.n_pop * SBLM_NPAR * blocks);
     const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
     const int k_next = st.scratch(sizeof(unsigned));
+    const int k_genes = st.scratch(sizeof(double) * SBLM_NPAR * (size_t)n_lc);
+    const int polish_blocks = std::min(n_lc, 2 * sms);
+    const unsigned pq = params->polish_fev > 0 ? polish_queue_capacity(mode, max_ep) : 0;
+    const int k_pq = st.scratch(deferred_entry_bytes() * (size_t)pq * polish_blocks);
+    if (params->polish_fev > 0 && polish_smem_bytes(mode, max_ep) > kPolishSmemBudget)
+        return fail(SBLM_EINVAL, "the amoeba polish stages at most %zu bytes of epochs (longest lightcurve %d)",
+                    kPolishSmemBudget, max_ep);
     if (n_seed < 0 || n_seed > c.n_pop) return fail(SBLM_EINVAL, "n_seed must be in [0, n_pop]");
+    if (params->polish_fev < 0 || params->polish_fev > kPolishMaxFev)
+        return fail(SBLM_EINVAL, "polish_fev must be in [0, %d]", kPolishMaxFev);
     if (n_seed > 0 && !seed_genes && !k_extra) return fail(SBLM_EINVAL, "seed_genes is NULL");
     int i_seed = -1;
     if (seed_genes) SBLM_TRY(st.arg(seed_genes, sizeof(double) * SBLM_NPAR * (size_t)n_lc * n_seed, true, false, &i_seed));
@@ -312,7 +342,28 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.max_ep = max_ep;
     a.seed = i_seed >= 0 ? static_cast<const double*>(st.dev(i_seed)) : nullptr;
     a.n_seed = n_seed;
+    a.polish_fev = params->polish_fev;
+    a.best_genes = static_cast<double*>(st.scratch_ptr(k_genes));
     out->a = a;
+    PolishArgs pa{};
+    pa.t = a.t;
+    pa.flux = a.flux;
+    pa.sigma = a.sigma;
+    pa.offsets = a.offsets;
+    pa.n_lc = n_lc;
+    pa.b = b;
+    pa.g_in = a.best_genes;
+    pa.g_stride = SBLM_NPAR;
+    pa.c_in = a.best_chi2;
+    pa.c_stride = 1;
+    pa.g_out = a.best_genes;
+    pa.c_out = a.best_chi2;
+    pa.maxfev = params->polish_fev;
+    pa.queue = static_cast<Deferred*>(st.scratch_ptr(k_pq));
+    pa.qcap = pq;
+    out->pa = pa;
+    out->polish_blocks = polish_blocks;
+    out->max_ep = max_ep;
     out->blocks = blocks;
     out->threads = threads;
     out->smem = smem;
@@ -323,6 +374,7 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
 sblm_status run_graph(const Prepared& p, cudaStream_t s) {
     // the cache key: every launch argument (the graph replays exactly this launch)
     std::vector<unsigned char> key(sizeof(BatchArgs) + sizeof(int) * 3 + sizeof(size_t));
+    // (the polish arguments are all derived from BatchArgs, whose bytes the key holds)
     unsigned char* w = key.data();
     std::memcpy(w, &p.a, sizeof(BatchArgs));
     w += sizeof(BatchArgs);
@@ -339,6 +391,7 @@ sblm_status run_graph(const Prepared& p, cudaStream_t s) {
             g_graph.exec = nullptr;
         }
         SBLM_CUDA(launch_batch(p.mode, p.a, p.blocks, p.threads, p.smem, s, true));
+        if (p.a.polish_fev > 0) SBLM_CUDA(polish_prepare(p.mode, p.max_ep));
         cudaStream_t cap;
         SBLM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph;
@@ -346,6 +399,14 @@ sblm_status run_graph(const Prepared& p, cudaStream_t s) {
         if (e == cudaSuccess) {
             cudaError_t e1 = cudaMemsetAsync(p.a.next, 0, sizeof(unsigned), cap);
             cudaError_t e2 = launch_batch(p.mode, p.a, p.blocks, p.threads, p.smem, cap, false);
+            if (e2 == cudaSuccess && p.a.polish_fev > 0) {
+                e2 = launch_polish(p.mode, p.pa, p.polish_blocks, p.max_ep, cap);
+                if (e2 == cudaSuccess) {
+                    genes_to_theta_kernel<<<(p.a.n_lc + 127) / 128, 128, 0, cap>>>(p.a.best_genes, p.a.n_lc, p.a.b,
+                                                                                 p.a.best_theta);
+                    e2 = cudaGetLastError();
+                }
+            }
             e = cudaStreamEndCapture(cap, &graph);
             if (e == cudaSuccess && (e1 != cudaSuccess || e2 != cudaSuccess)) {
                 cudaGraphDestroy(graph);

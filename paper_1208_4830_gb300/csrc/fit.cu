@@ -7,6 +7,7 @@
 
 #include "ea_launch.cuh"
 #include "forward_launch.cuh"
+#include "polish_launch.cuh"
 #include "runtime.cuh"
 
 namespace sblm {
@@ -32,7 +33,7 @@ void put(std::vector<unsigned char>& k, const V& v) {
 }
 
 std::vector<unsigned char> fit_graph_key(const EAConst& c, const ForwardArgs& fa, int n_gen, const double* tr,
-                                         const double* th, const double* chi, const double* P0) {
+                                         const double* th, const double* chi, const double* P0, int polish_fev) {
     std::vector<unsigned char> k;
     put(k, c.n_pop), put(k, c.n_par), put(k, c.n_tourn), put(k, c.stag_window), put(k, c.restart_after);
     put(k, c.p_mut0), put(k, c.stag_rel), put(k, c.seed), put(k, c.stream);
@@ -40,6 +41,7 @@ std::vector<unsigned char> fit_graph_key(const EAConst& c, const ForwardArgs& fa
     put(k, fa.G), put(k, fa.chi2_out), put(k, fa.queue), put(k, fa.queue_count), put(k, fa.queue_cap);
     for (int j = 0; j < SBLM_NPAR; ++j) put(k, fa.bounds.lo[j]), put(k, fa.bounds.hi[j]);
     put(k, n_gen), put(k, tr), put(k, th), put(k, chi), put(k, P0);
+    put(k, polish_fev);
     int dev = 0;
     cudaGetDevice(&dev);
     put(k, dev);
@@ -75,6 +77,11 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     if (!best_theta || !best_chi2) return fail(SBLM_EINVAL, "best_theta and best_chi2 are required");
     Bounds b;
     SBLM_TRY(check_bounds(bounds, &b));
+    const int polish_fev = params->polish_fev;
+    if (polish_fev < 0 || polish_fev > kPolishMaxFev)
+        return fail(SBLM_EINVAL, "polish_fev must be in [0, %d]", kPolishMaxFev);
+    if (polish_fev > 0 && polish_smem_bytes(params->precision, n_ep) > kPolishSmemBudget)
+        return fail(SBLM_EINVAL, "the amoeba polish stages at most %zu bytes of epochs (n_ep=%d)", kPolishSmemBudget, n_ep);
     const int n_pop = c.n_pop, n_gen = params->n_gen, m = n_pop * SBLM_NPAR;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CallLock lock;
@@ -145,13 +152,33 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
                 cur ^= 1;
             }
         }
+        if (e == cudaSuccess && polish_fev > 0) {  // amoeba fine-tuning of the archive's best
+            PolishArgs pa{};
+            pa.t = fa.t;
+            pa.flux = fa.flux;
+            pa.sigma = fa.sigma;
+            pa.offsets = nullptr;
+            pa.n_ep = n_ep;
+            pa.n_lc = 1;
+            pa.b = b;
+            pa.g_in = state->best_genes;
+            pa.g_stride = SBLM_MAX_NPAR;
+            pa.c_in = &state->best_chi2;
+            pa.c_stride = 1;
+            pa.g_out = state->best_genes;
+            pa.c_out = &state->best_chi2;
+            pa.maxfev = polish_fev;
+            pa.queue = static_cast<Deferred*>(fa.queue);
+            pa.qcap = fa.queue_cap;
+            e = launch_polish(fa.mode, pa, 1, n_ep, q);
+        }
         if (e == cudaSuccess) {
             finish_kernel<<<1, 32, 0, q>>>(state, b, th_out, chi_out);
             e = cudaGetLastError();
         }
         return e;
     };
-    SBLM_TRY(run_cached_graph(fit_graph_key(c, fa, n_gen, tr, th_out, chi_out, P[0]), enqueue, s));
+    SBLM_TRY(run_cached_graph(fit_graph_key(c, fa, n_gen, tr, th_out, chi_out, P[0], polish_fev), enqueue, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));
     return SBLM_OK;

@@ -1,0 +1,43 @@
+// polish_launch.cuh -- host interface of the amoeba fine-tuning kernel (polish.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "forward.cuh"
+#include "forward_launch.cuh"
+
+namespace sblm {
+
+constexpr int kPolishThreads = 256;
+constexpr int kPolishMaxFev = 1 << 20;
+constexpr size_t kPolishSmemBudget = 200 * 1024;
+
+struct PolishArgs {
+    const double* t;
+    const double* flux;
+    const double* sigma;
+    const int64_t* offsets;  // null: one lightcurve of n_ep epochs
+    int n_ep;
+    int n_lc;
+    Bounds b;
+    const double* g_in;  // start genes of lightcurve l at g_in[l * g_stride]
+    int g_stride;
+    const double* c_in;  // their chi^2 at c_in[l * c_stride], or null (evaluated)
+    int c_stride;
+    double* g_out;       // may alias g_in
+    double* c_out;       // may alias c_in
+    int maxfev;
+    Deferred* queue;     // MIXED: qcap entries per block
+    unsigned qcap;
+};
+
+size_t polish_smem_bytes(int mode, int max_ep);
+unsigned polish_queue_capacity(int mode, int max_ep);
+cudaError_t launch_polish(int mode, const PolishArgs& a, int blocks, int max_ep, cudaStream_t s);
+// set the kernel's shared-memory opt-in for `max_ep` (call before a stream capture)
+cudaError_t polish_prepare(int mode, int max_ep);
+
+}  // namespace sblm

@@ -226,7 +226,7 @@ void sblm_ea_params_default(sblm_ea_params* p) {
     p->stag_rel = 0.01;
     p->restart_after = 10;
     p->precision = SBLM_MIXED;
-    p->reserved = 0;
+    p->polish_fev = 0;
     p->seed = 0;
 }
 

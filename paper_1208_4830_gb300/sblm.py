@@ -44,7 +44,7 @@ class EAParams(ctypes.Structure):
         ("stag_rel", ctypes.c_double),
         ("restart_after", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("polish_fev", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
     ]
 
@@ -119,6 +119,10 @@ _SIGS = {
         ctypes.c_int,
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p,
          ctypes.c_double, _p, _p, _p],
+    ),
+    "sblm_polish_batch": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), _p, _i32, _i32, _p, _p, _p],
     ),
     "sblm_cnn_train_params_default": (None, [ctypes.POINTER(CnnTrainParams)]),
     "sblm_cnn_num_params": (ctypes.c_int32, []),
@@ -416,6 +420,20 @@ def autotune_batch(t, flux, sigma, offsets, lo, hi, p, trial_generations=2, stre
         except OSError:
             pass
     return best
+
+
+def polish_batch(t, flux, sigma, offsets, lo, hi, genes, maxfev, precision="mixed", stream=None):
+    """Amoeba fine-tuning of start genes [n_lc, 6]: (polished genes, chi^2)."""
+    n_lc = int(offsets.shape[0]) - 1
+    b = bounds(lo, hi)
+    g_out = np.empty((n_lc, 6))
+    c_out = np.empty(n_lc)
+    a = [_ptr(x) for x in (t, flux, sigma, offsets, genes)]
+    s = _stream(stream, t, flux, sigma, genes)
+    st = _lib.sblm_polish_batch(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), a[4][0], int(maxfev),
+                                _precision(precision), g_out.ctypes.data, c_out.ctypes.data, s)
+    _check(st, "sblm_polish_batch")
+    return g_out, c_out
 
 
 def fit_batch_cnn(t, flux, sigma, offsets, lo, hi, p, weights, seed_frac=0.5, tuning=None, stream=None):

@@ -176,3 +176,26 @@ def seasonal_batch(n_lc=512, seed=0, n_min=200, n_max=5000, span=(-300.0, 300.0)
         truths.append(th)
     return Batch(t=np.concatenate(ts), z=np.concatenate(zs), sigma_frac=np.concatenate(ss),
                  offsets=np.array(offs, dtype=np.int64), truth=np.array(truths))
+
+
+def heldout_batch(n_lc=2000, seed=0, n_ep=500, sigma_frac=0.02, caustic_frac=0.1, lo=-60.0, hi=60.0):
+    """Held-out lightcurves for the learned proposal: truths from the sweep priors with a fraction
+    re-aimed through a caustic (rows whose re-aimed t0 or u0 leaves the fit domain FIT_LO..FIT_HI
+    are dropped and drawn again, so every truth is reachable by the fitter), n_ep epochs uniform
+    in [lo, hi] d per curve, noise of sigma_frac of the true flux."""
+    rows = []
+    k = 0
+    while len(rows) < n_lc:
+        theta = prior_theta(n_lc, seed + 7919 * k)
+        theta, _, _ = force_caustics(theta, caustic_frac, seed + 1 + 7919 * k)
+        genes = theta.copy()
+        genes[:, 5] = np.log10(genes[:, 5])
+        inside = np.all((genes >= FIT_LO) & (genes <= FIT_HI), axis=1)
+        rows.extend(theta[inside][: n_lc - len(rows)])
+        k += 1
+    theta = np.array(rows)
+    g = _rng(seed + 2)
+    t = np.sort(g.uniform(lo, hi, (n_lc, n_ep)), axis=1).ravel()
+    z = g.standard_normal(n_lc * n_ep)
+    offsets = np.arange(n_lc + 1, dtype=np.int64) * n_ep
+    return Batch(t=t, z=z, sigma_frac=np.full(n_lc * n_ep, sigma_frac), offsets=offsets, truth=theta)
