@@ -129,11 +129,12 @@ sblm_status sblm_cnn_train(float* weights, float* adam_state, const sblm_cnn_tra
                            int64_t first_step, int32_t n_run, float* loss_history, void* stream);
 
 /*
- * Seed rows from the network's outputs: row r of lightcurve l draws y = mu + exp(s / 2) n with n
- * six Box-Muller deviates of Philox blocks (0, 10, r, 0..1) under key (seed, l), maps them to
- * physical parameters with the curve's window (t0 = c + h y0, tE = h e^{y1}, u0 = y2, alpha =
- * 2 pi y3 wrapped to [0, 2 pi), d = e^{y4}, log10 q = y5) and encodes them as genes over `bounds`
- * (Eq. (EMMA-encoding)), clamped to [0, 1]; a non-finite gene becomes 0.5.
+ * Seed rows from the network's outputs (draw round 0): row 0 of lightcurve l is the network's
+ * mean; row r >= 1 draws y = mu + exp(s / 2) n with n six Box-Muller deviates of Philox blocks
+ * (0, 10, r, 0..1) under key (seed, l). y is mapped to physical parameters with the curve's window
+ * (t0 = c + h y0, tE = h e^{y1}, u0 = y2, alpha = 2 pi y3 wrapped to [0, 2 pi), d = e^{y4},
+ * log10 q = y5) and encoded as genes over `bounds` (Eq. (EMMA-encoding)), clamped to [0, 1]; a
+ * non-finite gene becomes 0.5.
  *   out [n_lc][12], window [n_lc][2]; genes [n_lc][n_seed][6] FP64.
  */
 sblm_status sblm_cnn_propose(const float* out, const double* window, int32_t n_lc,
@@ -153,10 +154,12 @@ sblm_status sblm_fit_batch_seeded(const double* t, const double* flux, const dou
                                   double* best_chi2, void* stream);
 
 /*
- * The proposal-seeded batched fit in one call: sblm_cnn_bin, sblm_cnn_forward and
- * sblm_cnn_propose (seed = params->seed) on the device, then sblm_fit_batch_seeded with
- * n_seed = round(seed_frac * n_pop) rows per population. weights NULL or seed_frac 0 gives the
- * paper's fitter. 0 <= seed_frac <= 1.
+ * The proposal-seeded batched fit in one call: sblm_cnn_bin and sblm_cnn_forward on the device,
+ * then the batched fit with n_seed = round(seed_frac * n_pop) proposal rows in place of the last
+ * n_seed random rows of each population. The rows of the first population are those of
+ * sblm_cnn_propose (seed = params->seed); the k-th restart of a population draws its rows afresh
+ * from the same outputs in draw round k. weights NULL or seed_frac 0 gives the paper's fitter.
+ * 0 <= seed_frac <= 1.
  */
 sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, const double* sigma,
                                const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,

@@ -235,23 +235,25 @@ def adamw(w, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4
     return w - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def propose_genes(out, window, lo, hi, n_seed, seed):
-    """Seed rows for lightcurve l: y = mu + exp(s / 2) n with n standard normal (key (seed, l),
-    counter (0, OP_CNN_SAMPLE, row, block)), mapped from window units to physical parameters
-    (t0 = c + h y0, tE = h e^{y1}, u0 = y2, alpha = 2 pi y3 wrapped to [0, 2 pi), d = e^{y4},
-    log10 q = y5), then to genes (v - lo) / (hi - lo) clamped to [0, 1]; a non-finite gene is 0.5.
-    Returns [n_lc, n_seed, 6]."""
+def propose_genes(out, window, lo, hi, n_seed, seed, round=0):
+    """Seed rows for lightcurve l in draw round `round` (0: the first population, k: the k-th
+    restart): row 0 is the network's mean; row r >= 1 draws y = mu + exp(s / 2) n with n six
+    standard normal deviates (key (seed, l), counter (round, OP_CNN_SAMPLE, r, block)). y is
+    mapped from window units to physical parameters (t0 = c + h y0, tE = h e^{y1}, u0 = y2,
+    alpha = 2 pi y3 wrapped to [0, 2 pi), d = e^{y4}, log10 q = y5), then to genes
+    (v - lo) / (hi - lo) clamped to [0, 1]; a non-finite gene is 0.5. Returns [n_lc, n_seed, 6]."""
     out = np.asarray(out, dtype=np.float64)
     n_lc = out.shape[0]
     G = np.zeros((n_lc, n_seed, 6))
     rows = np.arange(n_seed)
     for l in range(n_lc):
-        ra = ph.philox4x64(0, OP_CNN_SAMPLE, rows, 0, seed, l)
-        rb = ph.philox4x64(0, OP_CNN_SAMPLE, rows, 1, seed, l)
+        ra = ph.philox4x64(round, OP_CNN_SAMPLE, rows, 0, seed, l)
+        rb = ph.philox4x64(round, OP_CNN_SAMPLE, rows, 1, seed, l)
         n = np.empty((n_seed, 6))
         n[:, 0], n[:, 1] = box_muller(ra[:, 0], ra[:, 1])
         n[:, 2], n[:, 3] = box_muller(ra[:, 2], ra[:, 3])
         n[:, 4], n[:, 5] = box_muller(rb[:, 0], rb[:, 1])
+        n[0] = 0.0
         mu, s = out[l, :6], out[l, 6:]
         y = mu + np.exp(0.5 * s) * n
         c, h = window[l]

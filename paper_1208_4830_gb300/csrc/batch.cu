@@ -21,6 +21,7 @@
 #include "ea_launch.cuh"
 #include "forward_run.cuh"
 #include "polish_launch.cuh"
+#include "proposal.cuh"
 #include "runtime.cuh"
 
 namespace sblm {
@@ -54,6 +55,9 @@ struct BatchArgs {
     int max_ep;        // longest lightcurve the staging area holds
     const double* seed;  // [n_lc][n_seed][6] genes of the seeded rows, or null
     int n_seed;          // rows n_pop - n_seed .. n_pop - 1 of the first population
+    const float* prop_out;    // proposal outputs [n_lc][12] and windows [n_lc][2]: seeded rows are drawn
+    const double* prop_win;   // here, afresh at every restart (else `seed` fills the first population)
+    uint64_t prop_seed;
     int polish_fev;      // amoeba fine-tuning of the archive's best (0: none), a separate launch
     double* best_genes;  // [n_lc][6] genes of best_chi2
 };
@@ -102,9 +106,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
         block_init_values(c, 0, keys, m, Pb[0], 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key), a.n2);
         if (a.n_seed > 0) {  // proposal rows replace the last n_seed random rows
             __syncthreads();
-            const double* sg = a.seed + (size_t)lc * a.n_seed * n_par;
             double* dst = Pb[0] + (size_t)(n_pop - a.n_seed) * n_par;
-            for (int e = threadIdx.x; e < a.n_seed * n_par; e += blockDim.x) dst[e] = sg[e];
+            if (a.prop_out) {
+                for (int r = threadIdx.x; r < a.n_seed; r += blockDim.x)
+                    proposal_row(a.prop_out + 12 * (size_t)lc, a.prop_win[2 * lc], a.prop_win[2 * lc + 1], a.b,
+                                 a.prop_seed, (uint64_t)lc, (uint64_t)r, 0, dst + (size_t)r * n_par);
+            } else {
+                const double* sg = a.seed + (size_t)lc * a.n_seed * n_par;
+                for (int e = threadIdx.x; e < a.n_seed * n_par; e += blockDim.x) dst[e] = sg[e];
+            }
         }
         if (threadIdx.x == 0) state_reset(c, s_state);
         __syncthreads();
@@ -159,6 +169,14 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 __syncthreads();
                 block_init_values(c, gen + 1, keys, m, next, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
                                   a.n2);
+                if (a.prop_out && a.n_seed > 0) {  // the restart draws fresh proposal rows
+                    __syncthreads();
+                    double* dst = next + (size_t)(n_pop - a.n_seed) * n_par;
+                    for (int r = threadIdx.x; r < a.n_seed; r += blockDim.x)
+                        proposal_row(a.prop_out + 12 * (size_t)lc, a.prop_win[2 * lc], a.prop_win[2 * lc + 1], a.b,
+                                     a.prop_seed, (uint64_t)lc, (uint64_t)r, (uint64_t)s_state.n_restarts,
+                                     dst + (size_t)r * n_par);
+                }
             } else {
                 if (threadIdx.x == 0) {
                     const double* e = Pb[cur] + (size_t)s_idx[0] * n_par;
@@ -480,7 +498,9 @@ extern "C" sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, c
     const cnn::InferScratch sc = cnn::infer_scratch_carve(st.scratch_ptr(k_inf), n_lc, n_seed);
     SBLM_CUDA(cnn::launch_seed_rows(p.a.t, p.a.flux, p.a.sigma, p.a.offsets, n_lc,
                                     static_cast<const float*>(st.dev(i_w)), p.a.b, n_seed, params->seed, sc, s));
-    p.a.seed = sc.genes;
+    p.a.prop_out = sc.out;
+    p.a.prop_win = sc.window;
+    p.a.prop_seed = params->seed;
     SBLM_TRY(run_graph(p, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));
