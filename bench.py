@@ -7,6 +7,9 @@ magnification, chi^2), then ranked, selected, reproduced and mutated into the ne
 Every step starts from the same population, so the work per step is fixed.
 
 Metric: binary-lens magnifications per second (candidates x epochs per step / step time).
+The JSON line also carries the fits/s comparison (unless --no-fits): the learned proposal trained
+on the device, then the proposal-seeded MIXED batched fitter, the plain MIXED fitter and the plain
+FP64 fitter (each EA + amoeba polish) on held-out synthetic curves, with their success rates.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
     python bench.py --impl reference ...   # the CPU oracle on the host cores, bounded sample
@@ -243,37 +246,96 @@ def make_device_step(sblm, P_in, t, flux, sigma, precision, dev):
     return step
 
 
-FIT_LCS, FIT_POP, FIT_GEN = 32, 512, 150
+# fits: held-out synthetic curves (sweep priors, 10% aimed through caustics, truths inside the fit
+# domain), 500 epochs in [-60, 60] d, 2% noise; every arm runs the EA then the amoeba polish
+FIT_LCS, FIT_LCS_FP64, FIT_EP, FIT_POP, FIT_GEN, FIT_POLISH = 256, 152, 500, 1024, 200, 2000
+PROPOSAL_STEPS, PROPOSAL_BATCH = 1024, 1024  # 1,048,576 training curves
+SEED_FRAC = 0.5
+# algorithmic flop of one training sample: forward products 2 K N per output position, backward
+# the weight and input gradients (the first layer has no input gradient)
+CNN_FWD_FLOP = 2 * (256 * 10 * 64 + 128 * 320 * 64 + 64 * 320 * 64 + 32 * 320 * 64 + 2048 * 128 + 128 * 12)
+CNN_STEP_FLOP_PER_SAMPLE = 3 * CNN_FWD_FLOP - 2 * 256 * 10 * 64
+
+
+def _success(best, chi, chi_true, truth, n_ep):
+    """Shares of fits meeting: the paper's criterion delta chi^2 / nu < 1 (nu = n_ep - 6, Section
+    4.1), delta chi^2 <= 1, and the strict one (paper's criterion and every parameter within 10%:
+    t0 relative to tE, alpha relative to 2 pi, the others relative to their own value)."""
+    d = chi - chi_true
+    da = np.abs((best[:, 3] - truth[:, 3] + np.pi) % (2 * np.pi) - np.pi)
+    err = np.stack([np.abs(best[:, 0] - truth[:, 0]) / truth[:, 1], np.abs(best[:, 1] / truth[:, 1] - 1),
+                    np.abs(best[:, 2] / truth[:, 2] - 1), da / (2 * np.pi), np.abs(best[:, 4] / truth[:, 4] - 1),
+                    np.abs(best[:, 5] / truth[:, 5] - 1)], 1)
+    weak = d / (n_ep - 6) < 1
+    return {"dchi2_per_dof_lt_1": float(weak.mean()), "dchi2_le_1": float(np.mean(d <= 1.0)),
+            "strict": float(np.mean(weak & np.all(err < 0.1, axis=1)))}
 
 
 def run_fits(sblm, args):
-    """Fits per second of the persistent batched fitter on seasonal lightcurves, MIXED against
-    the plain FP64 EA on the same GPU, and the share of fits within delta chi^2 <= 1 of the
-    injected truth (the truth's chi^2 computed by the library in FP64)."""
+    """Fits per second of the persistent batched fitter (EA + amoeba polish) on held-out curves:
+    the proposal-seeded MIXED fitter, the plain MIXED fitter and the plain FP64 fitter, with their
+    success rates; and the proposal's training on the device (1M generated curves)."""
     import torch
 
     from paper_1208_4830_gb300 import synth
 
-    b = synth.seasonal_batch(FIT_LCS, seed=11, n_min=200, n_max=400, span=(-100.0, 100.0), season=80.0, gap=30.0)
-    A = np.concatenate([sblm.magnification(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]], "fp64")[0]
-                        for i in range(FIT_LCS)])
+    b = synth.heldout_batch(FIT_LCS, seed=77, n_ep=FIT_EP)
+    t_d = torch.tensor(b.t, device="cuda")
+    A = torch.cat([sblm.magnification(torch.tensor(b.truth[i : i + 1], device="cuda"),
+                                      t_d[b.offsets[i] : b.offsets[i + 1]], "fp64")[0] for i in range(FIT_LCS)])
+    A = A.cpu().numpy()
     flux, sigma = b.observe(A)
-    chi_true = np.array([sblm.chi2(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]],
-                                   flux[b.offsets[i] : b.offsets[i + 1]], sigma[b.offsets[i] : b.offsets[i + 1]],
-                                   "fp64")[0] for i in range(FIT_LCS)])
+    sl = [slice(b.offsets[i], b.offsets[i + 1]) for i in range(FIT_LCS)]
+    chi_true = np.array([sblm.chi2(b.truth[i : i + 1], b.t[s], flux[s], sigma[s], "fp64")[0]
+                         for i, s in enumerate(sl)])
     dev = [torch.tensor(x, device="cuda") for x in (b.t, flux, sigma, b.offsets)]
-    out = {"workload": f"{FIT_LCS} seasonal lightcurves, 200-400 epochs, sigma 0.5-5%, "
-                       f"N_pop {FIT_POP} x {FIT_GEN} generations, batched persistent fitter"}
-    for prec in ("mixed", "fp64"):
-        p = sblm.params(n_pop=FIT_POP, n_gen=FIT_GEN, precision=prec, seed=0)
+
+    # the proposal network, trained on the device on curves the forward model generates
+    w = sblm.cnn_init(0)
+    st = torch.zeros(2 * sblm.cnn_num_params(), device="cuda")
+    tp = sblm.cnn_train_params(batch=PROPOSAL_BATCH, n_steps=PROPOSAL_STEPS, warmup=100)
+    sblm.cnn_train(w, st, tp, 0, 2)  # graph capture and warm-up (two steps of the schedule)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = sblm.cnn_train(w, st, tp, 2, PROPOSAL_STEPS - 2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    step_s = train_s / (PROPOSAL_STEPS - 2)
+    cnn_flop = CNN_STEP_FLOP_PER_SAMPLE * PROPOSAL_BATCH
+    proposal = {
+        "training_curves": PROPOSAL_STEPS * PROPOSAL_BATCH, "train_s": train_s + 2 * step_s,
+        "curves_per_s": PROPOSAL_BATCH / step_s, "ms_per_step": step_s * 1e3,
+        "loss_first": float(np.mean(hist[:10])), "loss_last": float(np.mean(hist[-50:])),
+        "step": "generator (priors, forward model MIXED, noise, normalisation) + BF16 tensor-core forward and "
+                "backward + AdamW, one CUDA graph",
+        "tensor_tflops_whole_step": cnn_flop / step_s / 1e12,
+        "flop_per_sample": CNN_STEP_FLOP_PER_SAMPLE,
+    }
+
+    def arm(precision, frac, n_lc):
+        d = dev if n_lc == FIT_LCS else [torch.tensor(x, device="cuda") for x in (
+            b.t[: b.offsets[n_lc]], flux[: b.offsets[n_lc]], sigma[: b.offsets[n_lc]], b.offsets[: n_lc + 1])]
+        p = sblm.params(n_pop=FIT_POP, n_gen=FIT_GEN, precision=precision, seed=1, polish_fev=FIT_POLISH)
+        if precision != "fp64":  # graph capture outside the timed call (FP64 is timed once, cold graph)
+            sblm.fit_batch_cnn(*d, synth.FIT_LO, synth.FIT_HI, p, w, seed_frac=frac)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, chi = sblm.fit_batch(*dev, synth.FIT_LO, synth.FIT_HI, p)
+        best, chi = sblm.fit_batch_cnn(*d, synth.FIT_LO, synth.FIT_HI, p, w, seed_frac=frac)
+        torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        out[prec] = {"fits_per_s": FIT_LCS / dt, "seconds": dt,
-                     "success": float(np.mean(chi - chi_true <= 1.0)),
-                     "magnifications_per_s": FIT_POP * FIT_GEN * float(b.t.size) / dt}
-    out["speedup_mixed_over_fp64"] = out["mixed"]["fits_per_s"] / out["fp64"]["fits_per_s"]
+        return {"fits_per_s": n_lc / dt, "seconds": dt, "n_lightcurves": n_lc,
+                "success": _success(best, chi, chi_true[:n_lc], b.truth[:n_lc], FIT_EP),
+                "magnifications_per_s": FIT_POP * FIT_GEN * FIT_EP * n_lc / dt}
+
+    out = {"workload": f"held-out synthetic curves (sweep priors, 10% through caustics), {FIT_EP} epochs, "
+                       f"2% noise; N_pop {FIT_POP} x {FIT_GEN} generations + amoeba polish ({FIT_POLISH} "
+                       f"chi^2 evaluations); batched persistent fitter",
+           "success_criterion": "dchi2_per_dof_lt_1 (paper, Section 4.1); dchi2_le_1 and strict also reported",
+           "proposal": proposal}
+    out["seeded_mixed"] = arm("mixed", SEED_FRAC, FIT_LCS)
+    out["plain_mixed"] = arm("mixed", 0.0, FIT_LCS)
+    out["plain_fp64"] = arm("fp64", 0.0, FIT_LCS_FP64)
+    out["fits_per_s_seeded_mixed_over_plain_fp64"] = out["seeded_mixed"]["fits_per_s"] / out["plain_fp64"]["fits_per_s"]
     return out
 
 
