@@ -46,7 +46,8 @@ typedef struct {
     int32_t batch;       /* curves per optimiser step [256], 1..4096 */
     int32_t n_steps;     /* length of the learning-rate schedule [4096] */
     int32_t warmup;      /* linear warm-up steps [200], >= 0 */
-    int32_t precision;   /* forward model of the generator: SBLM_FP64/MIXED/FP32 [SBLM_MIXED] */
+    int32_t precision;   /* forward model of the generator: SBLM_FP64/MIXED/FP32 [SBLM_FP32: the
+                            training noise, 0.3-5%, dwarfs FP32's error near caustics] */
     double lr;           /* peak learning rate [2e-3]; cosine decay to 0.1 lr at n_steps */
     double beta1;        /* [0.9] */
     double beta2;        /* [0.999] */

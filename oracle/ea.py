@@ -16,7 +16,7 @@ Sequence per generation t (Appendix A, "basic evolutionary sequence"):
   creep then jump mutation of the offspring (Appendix A, "Creep and jump mutation");
   stagnation check, jump-rate boost/throttle, restart (Appendix A, "Stagnation checks").
 
-Readings where the paper is silent or loose (each listed in the design doc):
+Readings where the paper is silent or loose:
 * initialisation pairs element pi(2k) with pi(2k+1) of a random permutation pi of all
   N_pop*N_par elements; pi sorts the elements by a key made of the top 44 bits of one Philox
   word per element with the element index in the low 20 bits (so no two keys are equal and

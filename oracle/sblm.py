@@ -25,7 +25,7 @@ What it computes, in the paper's order (Rajpaul 2012, Section 2.2):
 7. total magnification A = sum_i A_i (flux of a unit, unblended source), and the chi^2 of
    Section 4.1, sum_k ((F_k - A_k) / sigma_k)^2.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 * the image count must be 3 or 5 (Section 2.2) and the parities must sum to -1 (image-counting
   theorem for two point lenses). When the residual test gives anything else, the 3 smallest
   residuals are kept, plus the 4th and 5th when both are below ``PAIR_TOL``, and the point is

@@ -128,7 +128,7 @@ def test_cnn_abi_layout_and_validation(built, tmp_path):
         T = built.CnnTrainParams
         assert got == [ctypes.sizeof(T), T.lr.offset, T.seed.offset]
     p = built.cnn_train_params()
-    assert (p.batch, p.n_steps, p.precision, p.lr, p.forced_frac) == (256, 4096, 1, 2e-3, 0.1)
+    assert (p.batch, p.n_steps, p.precision, p.lr, p.forced_frac) == (256, 4096, 2, 2e-3, 0.1)
     # rejected before any CUDA call
     assert lib.sblm_cnn_make_batch(0, 0, 0, 0.1, 1, None, None, None, None) == 1
     assert lib.sblm_cnn_make_batch(0, 0, 4, 1.5, 1, None, None, None, None) == 1
