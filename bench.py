@@ -306,7 +306,7 @@ def run_fits(sblm, args):
         "training_curves": PROPOSAL_STEPS * PROPOSAL_BATCH, "train_s": train_s + 2 * step_s,
         "curves_per_s": PROPOSAL_BATCH / step_s, "ms_per_step": step_s * 1e3,
         "loss_first": float(np.mean(hist[:10])), "loss_last": float(np.mean(hist[-50:])),
-        "step": "generator (priors, forward model MIXED, noise, normalisation) + BF16 tensor-core forward and "
+        "step": "generator (priors, forward model FP32, noise, normalisation) + BF16 tensor-core forward and "
                 "backward + AdamW, one CUDA graph",
         "tensor_tflops_whole_step": cnn_flop / step_s / 1e12,
         "flop_per_sample": CNN_STEP_FLOP_PER_SAMPLE,
@@ -438,7 +438,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
