@@ -131,8 +131,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
             for (int base = 0; base < n_pop; base += per_pass) {
                 const int cand = base + group;
                 const bool valid = cand < n_pop;
-                Cand k{};
-                if (valid) k = candidate<true>(Pb[cur], a.b, cand);
+                const Cand k = group_candidate<true>(Pb[cur], a.b, cand, valid, G);
                 double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, nullptr, nullptr, queue,
                                                         &s_qcount, a.qcap);
                 for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);

@@ -61,8 +61,7 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
     const bool valid = c < n_cand;
     const int seg = (n_ep + G - 1) / G;
     const int e0 = min(n_ep, g * seg), e1 = min(n_ep, e0 + seg);
-    Cand k{};
-    if (valid) k = candidate<FROM_GENES>(src, bounds, c);
+    const Cand k = group_candidate<FROM_GENES>(src, bounds, c, valid, G);
     double* A_row = (A_out && valid) ? A_out + (size_t)c * n_ep : nullptr;
     uint8_t* f_row = (flags && valid) ? flags + (size_t)c * n_ep : nullptr;
     double chi = eval_run<MODE, CHI2, STAGED>(k, valid, c, e0, e1, seg, lc, A_row, f_row, queue, queue_count,

@@ -72,6 +72,27 @@ __device__ __forceinline__ Cand candidate(const double* __restrict__ src, const 
     return k;
 }
 
+// The candidate of a group of G threads (G a power of two; groups are aligned to G within the
+// warp, or span whole warps when G > 32), decoded once per warp-part by its first lane and
+// broadcast by shuffles: the decode's FP64 exp10, sincos and division run on the slow FP64 pipe.
+// Every lane of the warp must call it.
+template <bool FROM_GENES>
+__device__ __forceinline__ Cand group_candidate(const double* __restrict__ src, const Bounds& b, int c, bool valid,
+                                                int G) {
+    const int lane = threadIdx.x & 31;
+    const int src_lane = G < 32 ? (lane & ~(G - 1)) : 0;
+    Cand k{};
+    if (lane == src_lane && valid) k = candidate<FROM_GENES>(src, b, c);
+    k.t0 = __shfl_sync(0xffffffffu, k.t0, src_lane);
+    k.inv_tE = __shfl_sync(0xffffffffu, k.inv_tE, src_lane);
+    k.u0 = __shfl_sync(0xffffffffu, k.u0, src_lane);
+    k.sa = __shfl_sync(0xffffffffu, k.sa, src_lane);
+    k.ca = __shfl_sync(0xffffffffu, k.ca, src_lane);
+    k.d = __shfl_sync(0xffffffffu, k.d, src_lane);
+    k.q = __shfl_sync(0xffffffffu, k.q, src_lane);
+    return k;
+}
+
 // s + x as an unevaluated pair (hi, lo) of floats: Knuth's two-sum, then renormalisation
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
     const float s = hi + x;
