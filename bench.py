@@ -340,6 +340,58 @@ def run_fits(sblm, args):
     out["smaller_budget"] = {"seeded_mixed": arm("mixed", SEED_FRAC, FIT_LCS, FIT_POP_SMALL, FIT_GEN_SMALL),
                              "plain_mixed": arm("mixed", 0.0, FIT_LCS, FIT_POP_SMALL, FIT_GEN_SMALL)}
     out["fits_per_s_seeded_mixed_over_plain_fp64"] = out["seeded_mixed"]["fits_per_s"] / out["plain_fp64"]["fits_per_s"]
+    out["paper_workload"] = run_paper_workload(sblm, w)
+    return out
+
+
+# the paper's own test shape (Section 4.2, noise-free): Table 1 ranges, 100 evenly spaced epochs over
+# t0 +- (2..3) tE, sigma 0.01 mag; success per number of peaks, EA + amoeba as in Table 2
+PAPER_LCS, PAPER_POP, PAPER_GEN = 256, 1000, 3000
+PAPER_TABLE2_EA_AMOEBA = {"1": [97, 100], "2": [98, 100], "3": [97, 98], "4": [94, 94]}  # strict, weak (%)
+
+
+def run_paper_workload(sblm, w):
+    import torch
+
+    from paper_1208_4830_gb300 import synth
+
+    b = synth.paper_batch(PAPER_LCS, seed=3)
+    t_d = torch.tensor(b.t, device="cuda")
+    A, peaks = [], []
+    for i in range(PAPER_LCS):
+        th = torch.tensor(b.truth[i : i + 1], device="cuda")
+        A.append(sblm.magnification(th, t_d[b.offsets[i] : b.offsets[i + 1]], "fp64")[0].cpu().numpy())
+        fine = torch.linspace(float(b.t[b.offsets[i]]), float(b.t[b.offsets[i + 1] - 1]), 3000, dtype=torch.float64,
+                              device="cuda")
+        peaks.append(min(4, synth.count_peaks(sblm.magnification(th, fine, "fp64")[0].cpu().numpy())))
+    A = np.concatenate(A)
+    peaks = np.array(peaks)
+    flux, sigma = A.copy(), b.sigma(A)
+    dev = [torch.tensor(x, device="cuda") for x in (b.t, flux, sigma, b.offsets)]
+    out = {"workload": f"{PAPER_LCS} noise-free curves of the paper's test (Table 1 ranges, 100 epochs, sigma 0.01 mag); "
+                       f"N_pop {PAPER_POP} x {PAPER_GEN} generations + amoeba ({FIT_POLISH} evaluations)",
+           "curves_per_peak_class": {str(k): int(np.sum(peaks == k)) for k in (1, 2, 3, 4)},
+           "paper_table2_ea_amoeba_strict_weak_pct": PAPER_TABLE2_EA_AMOEBA}
+    for label, frac in (("plain_mixed", 0.0), ("seeded_mixed", SEED_FRAC)):
+        p = sblm.params(n_pop=PAPER_POP, n_gen=PAPER_GEN, precision="mixed", seed=1, polish_fev=FIT_POLISH)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, chi = sblm.fit_batch_cnn(*dev, synth.PAPER_LO, synth.PAPER_HI, p, w, seed_frac=frac)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tr = b.truth
+        d = chi  # noise-free: the truth's chi^2 is 0
+        da = np.abs((best[:, 3] - tr[:, 3] + np.pi) % (2 * np.pi) - np.pi)
+        err = np.stack([np.abs(best[:, 0] - tr[:, 0]) / tr[:, 1], np.abs(best[:, 1] / tr[:, 1] - 1),
+                        np.abs(best[:, 2] / tr[:, 2] - 1), da / (2 * np.pi), np.abs(best[:, 4] / tr[:, 4] - 1),
+                        np.abs(best[:, 5] / tr[:, 5] - 1)], 1)
+        weak = d / (100 - 6) < 1
+        strict = weak & np.all(err < 0.1, axis=1)
+        out[label] = {"fits_per_s": PAPER_LCS / dt, "seconds": dt,
+                      "success_strict_weak_pct_by_peaks": {str(k): [round(100 * float(strict[peaks == k].mean()), 1),
+                                                                    round(100 * float(weak[peaks == k].mean()), 1)]
+                                                           for k in (1, 2, 3, 4)},
+                      "success_strict_weak_pct": [round(100 * float(strict.mean()), 1), round(100 * float(weak.mean()), 1)]}
     return out
 
 

@@ -46,8 +46,8 @@ typedef struct {
     int32_t batch;       /* curves per optimiser step [256], 1..4096 */
     int32_t n_steps;     /* length of the learning-rate schedule [4096] */
     int32_t warmup;      /* linear warm-up steps [200], >= 0 */
-    int32_t precision;   /* forward model of the generator: SBLM_FP64/MIXED/FP32 [SBLM_FP32: the
-                            training noise, 0.3-5%, dwarfs FP32's error near caustics] */
+    int32_t precision;   /* forward model of the generator: SBLM_FP64/MIXED/FP32 [SBLM_FP32: FP32's
+                            error near caustics is far below the noise of most training curves] */
     double lr;           /* peak learning rate [2e-3]; cosine decay to 0.1 lr at n_steps */
     double beta1;        /* [0.9] */
     double beta2;        /* [0.999] */
@@ -77,8 +77,8 @@ sblm_status sblm_cnn_init(float* weights, uint64_t seed, void* stream);
  * the trajectory is re-aimed through a caustic point (a root of the critical quartic
  * e^{i phi} z^2 (z - d)^2 - (1 + q) z^2 + 2 d z - d^2 mapped by the lens equation) crossed at
  * t' U[-0.8, 0.8]; magnification at the 256 bin centres s_j = -1 + (2 j + 1) / 256 by the forward
- * model in `precision`; flux A (1 + sigma z_j) with sigma log-U[0.003, 0.05] and z_j unit normal;
- * bins dropped with probability U[0, 0.3] and, half the time, a gap of up to 40% of the bins
+ * model in `precision`; flux A (1 + sigma z_j) with sigma log-U[1e-4, 0.05] and z_j unit normal;
+ * bins dropped with probability U[0, 0.7] and, half the time, a gap of up to 40% of the bins
  * (at least 16 bins are kept); then the input normalisation above.
  *   x [batch][256][2] FP32, y [batch][6] FP32 targets, theta [batch][6] FP64 parameters in
  *   window units (t0', tE', u0, alpha, d, q); theta may be NULL.
@@ -157,10 +157,9 @@ sblm_status sblm_fit_batch_seeded(const double* t, const double* flux, const dou
 /*
  * The proposal-seeded batched fit in one call: sblm_cnn_bin and sblm_cnn_forward on the device,
  * then the batched fit with n_seed = round(seed_frac * n_pop) proposal rows in place of the last
- * n_seed random rows of each population. The rows of the first population are those of
- * sblm_cnn_propose (seed = params->seed); the k-th restart of a population draws its rows afresh
- * from the same outputs in draw round k. weights NULL or seed_frac 0 gives the paper's fitter.
- * 0 <= seed_frac <= 1.
+ * n_seed random rows of each first population: the rows of sblm_cnn_propose (seed =
+ * params->seed). Restarts are the paper's random initialisation. weights NULL or seed_frac 0 gives
+ * the paper's fitter. 0 <= seed_frac <= 1.
  */
 sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, const double* sigma,
                                const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,

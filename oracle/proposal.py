@@ -46,8 +46,8 @@ LN_TE_RANGE = (math.log(0.04), math.log(1.5))
 LN_D_RANGE = (math.log(0.3), math.log(3.0))
 LOG10Q_RANGE = (-4.0, 0.0)
 T_CROSS_RANGE = (-0.8, 0.8)
-LN_SIGMA_RANGE = (math.log(0.003), math.log(0.05))
-DROP_MAX = 0.3
+LN_SIGMA_RANGE = (math.log(1e-4), math.log(0.05))
+DROP_MAX = 0.7
 GAP_PROB = 0.5
 GAP_MAX = 0.4
 MIN_KEPT = 16
@@ -236,8 +236,8 @@ def adamw(w, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4
 
 
 def propose_genes(out, window, lo, hi, n_seed, seed, round=0):
-    """Seed rows for lightcurve l in draw round `round` (0: the first population, k: the k-th
-    restart): row 0 is the network's mean; row r >= 1 draws y = mu + exp(s / 2) n with n six
+    """Seed rows for lightcurve l in draw round `round` (counter word 0; the fitter seeds its first
+    population with round 0): row 0 is the network's mean; row r >= 1 draws y = mu + exp(s / 2) n with n six
     standard normal deviates (key (seed, l), counter (round, OP_CNN_SAMPLE, r, block)). y is
     mapped from window units to physical parameters (t0 = c + h y0, tE = h e^{y1}, u0 = y2,
     alpha = 2 pi y3 wrapped to [0, 2 pi), d = e^{y4}, log10 q = y5), then to genes

@@ -55,8 +55,8 @@ struct BatchArgs {
     int max_ep;        // longest lightcurve the staging area holds
     const double* seed;  // [n_lc][n_seed][6] genes of the seeded rows, or null
     int n_seed;          // rows n_pop - n_seed .. n_pop - 1 of the first population
-    const float* prop_out;    // proposal outputs [n_lc][12] and windows [n_lc][2]: seeded rows are drawn
-    const double* prop_win;   // here, afresh at every restart (else `seed` fills the first population)
+    const float* prop_out;    // proposal outputs [n_lc][12] and windows [n_lc][2]: the seeded rows of the
+    const double* prop_win;   // first population are drawn here (else `seed` holds them)
     uint64_t prop_seed;
     int polish_fev;      // amoeba fine-tuning of the archive's best (0: none), a separate launch
     double* best_genes;  // [n_lc][6] genes of best_chi2
@@ -168,14 +168,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 __syncthreads();
                 block_init_values(c, gen + 1, keys, m, next, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
                                   a.n2);
-                if (a.prop_out && a.n_seed > 0) {  // the restart draws fresh proposal rows
-                    __syncthreads();
-                    double* dst = next + (size_t)(n_pop - a.n_seed) * n_par;
-                    for (int r = threadIdx.x; r < a.n_seed; r += blockDim.x)
-                        proposal_row(a.prop_out + 12 * (size_t)lc, a.prop_win[2 * lc], a.prop_win[2 * lc + 1], a.b,
-                                     a.prop_seed, (uint64_t)lc, (uint64_t)r, (uint64_t)s_state.n_restarts,
-                                     dst + (size_t)r * n_par);
-                }
             } else {
                 if (threadIdx.x == 0) {
                     const double* e = Pb[cur] + (size_t)s_idx[0] * n_par;

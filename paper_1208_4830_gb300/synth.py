@@ -199,3 +199,62 @@ def heldout_batch(n_lc=2000, seed=0, n_ep=500, sigma_frac=0.02, caustic_frac=0.1
     z = g.standard_normal(n_lc * n_ep)
     offsets = np.arange(n_lc + 1, dtype=np.int64) * n_ep
     return Batch(t=t, z=z, sigma_frac=np.full(n_lc * n_ep, sigma_frac), offsets=offsets, truth=theta)
+
+
+# Table 1 of the paper: the ranges of its simulated lightcurves and fits (d = a, u0 = b, alpha =
+# theta, t0 = t_m), as genes (t0, tE, u0, alpha, d, log10 q)
+PAPER_LO = np.array([-20.0, 5.0, 0.001, 0.0, 0.6, -1.0])
+PAPER_HI = np.array([20.0, 50.0, 1.0, 2.0 * np.pi, 1.7, 0.0])
+
+
+@dataclass
+class PaperBatch:
+    t: np.ndarray        # concatenated epochs
+    offsets: np.ndarray  # int64 [n_lc + 1]
+    truth: np.ndarray    # (n_lc, 6)
+    sigma_frac: float    # sigma of each flux point as a fraction of the true flux (noise-free curves)
+
+    def sigma(self, A_true):
+        return self.sigma_frac * np.asarray(A_true)
+
+
+# the paper's sigma of 0.01 (in magnitudes: it fits magnitudes with a baseline-magnitude
+# parameter) as a fraction of the flux, 0.4 ln(10) x 0.01
+PAPER_SIGMA_FRAC = 0.4 * np.log(10.0) * 0.01
+
+
+def paper_batch(n_lc=512, seed=0, n_ep=100):
+    """Noise-free test curves shaped like the paper's (Section 4.2): parameters uniform over the
+    Table 1 ranges (q uniform in [0.1, 1]), n_ep evenly spaced epochs from t_start to t_end with
+    (t_start - t0)/tE uniform in (-3, -2) and (t_end - t0)/tE uniform in (2, 3); the flux is the
+    magnification itself, with sigma = 0.01 mag (0.92% of the flux) for chi^2."""
+    g = _rng(seed)
+    u = g.uniform(size=(n_lc, 6))
+    v = PAPER_LO + (PAPER_HI - PAPER_LO) * u
+    theta = v.copy()
+    theta[:, 5] = 0.1 + 0.9 * u[:, 5]  # q uniform in [0.1, 1]
+    a = g.uniform(-3.0, -2.0, n_lc)
+    b = g.uniform(2.0, 3.0, n_lc)
+    ts = [np.linspace(th[0] + ai * th[1], th[0] + bi * th[1], n_ep) for th, ai, bi in zip(theta, a, b)]
+    offsets = np.arange(n_lc + 1, dtype=np.int64) * n_ep
+    return PaperBatch(t=np.concatenate(ts), offsets=offsets, truth=theta, sigma_frac=PAPER_SIGMA_FRAC)
+
+
+def count_peaks(A, rel_prominence=0.01):
+    """Peaks of a lightcurve sampled finely: local maxima that rise above the higher of the two
+    neighbouring minima by more than rel_prominence of their height."""
+    A = np.asarray(A, dtype=np.float64)
+    n = 0
+    for i in range(1, A.size - 1):
+        if A[i] > A[i - 1] and A[i] >= A[i + 1]:
+            left = A[: i + 1][::-1]
+            right = A[i:]
+            lmin = np.minimum.accumulate(left)
+            rmin = np.minimum.accumulate(right)
+            # walk down each side until a higher point appears (or the end)
+            li = np.argmax(left > A[i]) if np.any(left > A[i]) else left.size
+            ri = np.argmax(right > A[i]) if np.any(right > A[i]) else right.size
+            base = max(lmin[li - 1], rmin[ri - 1])
+            if A[i] - base > rel_prominence * A[i]:
+                n += 1
+    return n
