@@ -56,6 +56,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device):
+    """The largest of the ranks' values (every rank gets it); the value itself with one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, step_ms):
+    """Units per second of the whole job: every rank's units over the slowest rank's step time."""
+    return world * units_per_rank / step_ms * 1e3
+
+
 def sample_clocks_start(device_index):
     try:
         f = open(os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv") if os.path.isdir(
@@ -148,11 +165,7 @@ def run_gpu(args):
     clk = sample_clocks_stop(clocks)
     ms = [a.elapsed_time(b) for a, b in ev]
     fwd_ms = [a.elapsed_time(b) for a, b in fwd_ev]
-    step_ms = float(np.mean(ms))
-    if world > 1:
-        tt = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
+    step_ms = max_over_ranks(float(np.mean(ms)), dev)
 
     # end to end through the C ABI with host buffers: pinned host inputs, host results
     e2e = run_e2e(sblm, sw, P0, flux.cpu().numpy(), sigma.cpu().numpy(), args) if args.extras else None
@@ -179,7 +192,7 @@ def run_gpu(args):
     fits = run_fits(sblm, args) if (args.extras and args.fits) else None
 
     if rank == 0:
-        value = world * N_CAND * N_EP / step_ms * 1e3
+        value = whole_job_rate(world, N_CAND * N_EP, step_ms)
         fwd = float(np.mean(fwd_ms))
         prof = PROFILE.get(args.precision, {})
         flop = prof.get("flop_per_mag")
