@@ -492,6 +492,7 @@ extern "C" sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, c
     p.a.prop_out = sc.out;
     p.a.prop_win = sc.window;
     p.a.prop_seed = params->seed;
+    SBLM_TRY(cnn::check_timeout(s));
     SBLM_TRY(run_graph(p, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));

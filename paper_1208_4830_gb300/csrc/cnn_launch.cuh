@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "../../include/sblm.h"
 #include "forward_launch.cuh"
 
 namespace sblm {
@@ -30,6 +31,9 @@ InferScratch infer_scratch_carve(void* base, int n, int n_seed);
 cudaError_t launch_seed_rows(const double* t, const double* flux, const double* sigma, const int64_t* offsets,
                              int n_lc, const float* weights, const Bounds& b, int n_seed, uint64_t seed,
                              const InferScratch& sc, cudaStream_t s);
+
+// SBLM_ETIMEOUT if a tensor-core tile gave up waiting since the last check (synchronises s)
+sblm_status check_timeout(cudaStream_t s);
 
 }  // namespace cnn
 }  // namespace sblm
