@@ -215,7 +215,8 @@ def run_gpu(args):
             "by_precision": by_prec,
             "fits": fits,
             "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            # per step: forward_kernel (+ resolve_kernel in MIXED), rank_kernel, offspring_kernel
+            "gpu_launches": (4 if args.precision == "mixed" else 3) * args.steps,
             "clocks": clk,
             "wall_s": wall,
         }
