@@ -45,7 +45,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # ncu thread-level instruction counts (FMA counted as 2 flop), and the kernel's DRAM bytes per
 # launch, from the captures summarised in profiles/forward_kernel_<precision>_sweep_4096x2000.md
 PROFILE = {
-    "mixed": {"flop_per_mag": 2973.0, "traffic": 4.03e6, "file": "profiles/forward_kernel_mixed_sweep_4096x2000.md"},
+    "mixed": {"flop_per_mag": 2973.0, "traffic": 3.99e6, "file": "profiles/forward_kernel_mixed_sweep_4096x2000.md"},
 }
 
 
