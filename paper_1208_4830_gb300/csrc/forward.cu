@@ -60,7 +60,10 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
     const int c = blockIdx.x * per_block + group;
     const bool valid = c < n_cand;
     const int seg = (n_ep + G - 1) / G;
-    const int e0 = min(n_ep, g * seg), e1 = min(n_ep, e0 + seg);
+    // a candidate wider than a warp interleaves its segments across its warps (segment lane * G/32
+    // + warp), so each warp samples the whole lightcurve and the warps carry similar work
+    const int gs = G > 32 ? (g & 31) * (G >> 5) + (g >> 5) : g;
+    const int e0 = min(n_ep, gs * seg), e1 = min(n_ep, e0 + seg);
     const Cand k = group_candidate<FROM_GENES>(src, bounds, c, valid, G);
     double* A_row = (A_out && valid) ? A_out + (size_t)c * n_ep : nullptr;
     uint8_t* f_row = (flags && valid) ? flags + (size_t)c * n_ep : nullptr;
