@@ -245,3 +245,24 @@ def test_proposal_gain_on_heldout_curves(lib):
     d_plain, d_seed = fits(128, 20, 0.0), fits(128, 20, 0.5)
     assert np.median(d_seed) < np.median(d_plain), (np.median(d_seed), np.median(d_plain))
     assert np.mean(d_seed <= 1.0) >= np.mean(d_plain <= 1.0)
+
+
+def test_training_batch_size_properties(lib):
+    """At the training batch of 1024: network outputs of sampled rows against the FP64 oracle, and
+    the whole-batch gradient against the mean of the gradients of its eight 128-curve chunks (the
+    loss is a mean over curves; the 1/B scalings are powers of two, so the BF16 operands of each
+    curve are the same and only the FP32 summation order differs)."""
+    x, y, _ = lib.cnn_make_batch(seed=1, step=0, batch=1024, precision="fp32")
+    w = lib.cnn_init(seed=2)
+    out = lib.cnn_forward(w, x).cpu().numpy()
+    wn = w.cpu().numpy().astype(np.float64)
+    rows = [0, 137, 511, 1023]
+    ref, _ = ocnn.forward(wn, x[rows].cpu().numpy().astype(np.float64))
+    assert _rel(out[rows], ref) <= BF16_REL
+    L, g = lib.cnn_loss_grad(w, x, y)
+    parts = [lib.cnn_loss_grad(w, x[i * 128 : (i + 1) * 128].contiguous(), y[i * 128 : (i + 1) * 128].contiguous())
+             for i in range(8)]
+    Lm = np.mean([p[0] for p in parts])
+    gm = np.mean([p[1].cpu().numpy().astype(np.float64) for p in parts], axis=0)
+    assert L == pytest.approx(Lm, rel=1e-6)
+    assert _rel(g.cpu().numpy().astype(np.float64), gm) <= 1e-5
