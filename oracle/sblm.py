@@ -23,7 +23,9 @@ What it computes, in the paper's order (Rajpaul 2012, Section 2.2):
    modulus without the square (Section 2.2, the equation for A_i); the square is required for
    the Jacobian of the lens map and for the single-lens (Paczynski) limit;
 7. total magnification A = sum_i A_i (flux of a unit, unblended source), and the chi^2 of
-   Section 4.1, sum_k ((F_k - A_k) / sigma_k)^2.
+   Section 4.1, sum_k ((F_k - A_k) / sigma_k)^2;
+8. the blended model of Section 4.2, f A + (1 - f), with f profiled out in closed form
+   (``blend_fit``; flux normalised to the baseline).
 
 Readings where the paper is silent:
 * the image count must be 3 or 5 (Section 2.2) and the parities must sum to -1 (image-counting
@@ -40,7 +42,8 @@ Pinned by tests/test_oracle_forward.py: closed-form trajectory geometry, the len
 residual of every image, the 3-or-5 image count and parity sum, the Paczynski limit for q -> 0
 and for a -> 0, mirror symmetry, the far-field limit, a numerical Jacobian of the lens map at
 each image, a brute-force lens-equation image search that never touches the quintic, and
-inverse ray shooting on a small source.
+inverse ray shooting on a small source; the blended fit by its exact recovery of a blended
+curve, a brute-force scan over f, and its clamps.
 """
 from __future__ import annotations
 
@@ -284,6 +287,33 @@ def chi2_from_model(model, flux, sigma):
 def chi2(theta, t, flux, sigma):
     """chi^2 of each parameter row against the lightcurve (t, flux, sigma)."""
     return chi2_from_model(magnification(theta, t), flux, sigma)
+
+
+BLEND_F_MIN = 1e-3  # smallest blending fraction of the profiled fit
+
+
+def blend_fit(A, flux, sigma, f_min=BLEND_F_MIN):
+    """Blended model of Section 4.2 (Eq. blend), A_obs = f A + (1 - f), with the fraction f
+    profiled out: the paper notes that its least-squares value follows from a linear equation.
+    With a = A - 1, b = F - 1 and w = 1/sigma^2, chi^2(f) = sum w (b - f a)^2 is least at
+    f = sum w a b / sum w a^2, clamped to [f_min, 1]. Sums run over the last axis in order.
+    Returns (chi^2, f)."""
+    A = np.asarray(A, np.float64)
+    a = A - 1.0
+    b = np.asarray(flux, np.float64) - 1.0
+    w = 1.0 / np.asarray(sigma, np.float64) ** 2
+    s_ab = np.sum(w * a * b, axis=-1)
+    s_aa = np.sum(w * a * a, axis=-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = np.where(s_aa > 0.0, s_ab / s_aa, 1.0)
+    f = np.clip(f, f_min, 1.0)
+    r = b - f[..., None] * a
+    return np.sum(w * r * r, axis=-1), f
+
+
+def chi2_blend(theta, t, flux, sigma, f_min=BLEND_F_MIN):
+    """(chi^2, f) of each parameter row with the blending fraction profiled out."""
+    return blend_fit(magnification(theta, t), flux, sigma, f_min)
 
 
 def paczynski(u):

@@ -246,3 +246,33 @@ def test_caustic_forcing_crosses_a_caustic():
             _, info = S.magnification(row[None, :], t, return_info=True)
             changes = max(changes, np.abs(np.diff(info["n"][0])).sum())
         assert changes >= 2
+
+
+def test_blend_fit_recovers_a_blended_curve():
+    theta = np.array([[0.0, 20.0, 0.2, 0.7, 1.1, 0.3]])
+    t = np.linspace(-40, 40, 300)
+    A = S.magnification(theta, t)[0]
+    sigma = 0.01 * A
+    for f0 in (1.0, 0.6, 0.05):
+        flux = f0 * A + (1 - f0)
+        c, f = S.blend_fit(A, flux, sigma)
+        assert f == pytest.approx(f0, rel=1e-12) and c < 1e-18
+    # the closed form is the minimum of a brute-force scan over f
+    rng = np.random.default_rng(3)
+    flux = 0.4 * A + 0.6 + sigma * rng.standard_normal(t.size)
+    c, f = S.blend_fit(A, flux, sigma)
+    grid = np.linspace(0.001, 1.0, 20001)
+    scan = [np.sum(((flux - (g * A + 1 - g)) / sigma) ** 2) for g in grid]
+    assert c <= min(scan) + 1e-9 and abs(f - grid[int(np.argmin(scan))]) < 1e-4
+    assert c == pytest.approx(S.chi2_from_model(f * A + 1 - f, flux, sigma), rel=1e-12)
+
+
+def test_blend_fit_clamps():
+    A = np.array([1.0, 2.0, 5.0, 2.0, 1.0])
+    sigma = np.full(5, 0.1)
+    c, f = S.blend_fit(A, 2.0 * (A - 1) + 1, sigma)  # needs f = 2: clamped to 1
+    assert f == 1.0 and c == pytest.approx(np.sum(((A - 1) / 0.1) ** 2))
+    c, f = S.blend_fit(A, 1 - 0.5 * (A - 1), sigma)  # anti-correlated: clamped to f_min
+    assert f == S.BLEND_F_MIN
+    c, f = S.blend_fit(np.ones(5), np.ones(5) * 1.1, sigma)  # flat model: f = 1 by convention
+    assert f == 1.0 and c == pytest.approx(5 * 1.0)
