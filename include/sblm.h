@@ -55,6 +55,16 @@ enum {
     SBLM_FP32 = 2   /* FP32 solve, no FP64 re-solve; chi^2 accumulated in FP64 */
 };
 
+/* OR-ed into sblm_ea_params.precision of the batched fitters (sblm_fit_batch*), or into the
+ * precision argument of sblm_polish_batch: each candidate's chi^2 is that of the blended model
+ * f A + (1 - f) (Section 4.2, Eq. blend; flux normalised to the baseline) with f profiled out as
+ * in sblm_chi2_blend, so best_chi2 / chi2_out hold that chi^2 and the six returned parameters
+ * are those of the lens; sblm_chi2_blend on them gives f. Needs 8 bytes of device scratch per
+ * epoch per population row per SM. The single-lightcurve calls (sblm_fit, sblm_ea_*) reject it
+ * with SBLM_EINVAL. */
+#define SBLM_BLEND 16
+#define SBLM_BLEND_F_MIN 1e-3 /* smallest profiled blending fraction */
+
 #define SBLM_NPAR 6        /* SBLM genes */
 #define SBLM_MAX_NPAR 16   /* largest N_par accepted by the generic EA calls */
 #define SBLM_MAX_WINDOW 15 /* largest stagnation window */
@@ -258,6 +268,22 @@ sblm_status sblm_autotune_batch(const double* t, const double* flux, const doubl
                                 sblm_batch_tuning* best, double* best_ms, void* stream);
 
 /*
+ * chi^2 of the blended model of Section 4.2 (Eq. blend), A_obs = f A + (1 - f), for each
+ * parameter row, with the blending fraction profiled out: the paper notes its least-squares value
+ * follows from a linear equation. With a_k = A_k - 1, b_k = F_k - 1 and w_k = 1/sigma_k^2,
+ * f = sum w a b / sum w a^2 clamped to [SBLM_BLEND_F_MIN, 1] (f = 1 when sum w a^2 = 0), and
+ * chi^2 = sum w (b - f a)^2; the sums run per candidate in FP64, in a fixed order (one warp per
+ * candidate, epochs strided over its lanes, then a shuffle tree), so results are reproducible.
+ * A is computed as by sblm_magnification in `precision` (SBLM_FP64, SBLM_MIXED or SBLM_FP32).
+ *   chi2_out [n_cand]; f_out [n_cand] (may be NULL). n_ep = 0 gives chi^2 = 0 and f = 1.
+ *   Uses n_cand * n_ep * 8 bytes of device scratch. Errors: SBLM_EINVAL for negative sizes,
+ *   NULL buffers, an unknown precision or non-finite host inputs.
+ */
+sblm_status sblm_chi2_blend(const double* theta, int32_t n_cand, const double* t, const double* flux,
+                            const double* sigma, int32_t n_ep, double* chi2_out, double* f_out,
+                            int32_t precision, void* stream);
+
+/*
  * Amoeba fine-tuning (Section 4.1: the EA "with amoeba"; Nelder & Mead 1965 with the standard
  * coefficients of Lagarias et al. 1998) of given solutions: for each lightcurve (layout of
  * sblm_fit_batch), a downhill-simplex search in the genes over `bounds` starting from
@@ -265,7 +291,7 @@ sblm_status sblm_autotune_batch(const double* t, const double* flux, const doubl
  * reflection 1, expansion 2, contraction 1/2, shrink 1/2, trial points clamped to [0, 1], the
  * simplex rebuilt around its best vertex whenever it has collapsed to 1e-9, stopped after
  * `maxfev` chi^2 evaluations (a step in progress may take up to 6 more). The chi^2 is that of
- * sblm_chi2_genes in `precision`. genes_out [n_lc * 6] (may alias genes_in) receives the best
+ * sblm_chi2_genes in `precision` (| SBLM_BLEND: of the blended model). genes_out [n_lc * 6] (may alias genes_in) receives the best
  * vertex, chi2_out [n_lc] its chi^2. The longest lightcurve must fit 200 KB of shared memory
  * (24 bytes per epoch in FP64, 16 otherwise). 0 <= maxfev <= 2^20.
  */

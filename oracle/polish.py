@@ -98,12 +98,15 @@ def nelder_mead(fun, x0, f0=None, maxfev=1000, delta=DELTA):
     return x0, f_start, fev
 
 
-def polish_sblm(t, flux, sigma, lo, hi, genes, maxfev, chi2_start=None):
-    """Amoeba fine-tuning of one SBLM solution given by its genes: (genes, chi^2, evaluations)."""
+def polish_sblm(t, flux, sigma, lo, hi, genes, maxfev, chi2_start=None, blend=False):
+    """Amoeba fine-tuning of one SBLM solution given by its genes: (genes, chi^2, evaluations).
+    With ``blend`` the objective is the chi^2 of the blended model of Section 4.2 with the
+    blending fraction profiled out (``sblm.chi2_blend``)."""
     from . import ea, sblm
 
     def fun(g):
-        c = sblm.chi2(ea.sblm_theta(np.asarray(g)[None, :], lo, hi), t, flux, sigma)[0]
+        theta = ea.sblm_theta(np.asarray(g)[None, :], lo, hi)
+        c = (sblm.chi2_blend(theta, t, flux, sigma)[0] if blend else sblm.chi2(theta, t, flux, sigma))[0]
         return c if math.isfinite(c) else math.inf
 
     return nelder_mead(fun, genes, chi2_start, maxfev)

@@ -19,6 +19,7 @@
 #include "../../include/sblm_cnn.h"
 #include "cnn_launch.cuh"
 #include "ea_launch.cuh"
+#include "blend.cuh"
 #include "forward_run.cuh"
 #include "polish_launch.cuh"
 #include "proposal.cuh"
@@ -60,7 +61,23 @@ struct BatchArgs {
     uint64_t prop_seed;
     int polish_fev;      // amoeba fine-tuning of the archive's best (0: none), a separate launch
     double* best_genes;  // [n_lc][6] genes of best_chi2
+    int blend;           // chi^2 of the blended model with f profiled out (Section 4.2)
+    double f_min;
+    double* A_scr;       // blend: per block n_pop x max_ep magnifications
 };
+
+// flux and weight 1/sigma of staged epoch e
+template <int MODE>
+__device__ __forceinline__ void staged_fw(const LCView& v, int e, double& F, double& w) {
+    if (MODE == SBLM_FP64) {
+        F = v.s_f[e];
+        w = v.s_w[e];
+    } else {
+        const float4 ep = v.s_ep[e];
+        F = ep.z;
+        w = ep.w;
+    }
+}
 
 size_t batch_smem_bytes(int mode, int n_pop, int n2, int max_ep) {
     const size_t ep = (size_t)max_ep * (mode == SBLM_FP64 ? 3 * sizeof(double) : sizeof(float4));
@@ -132,7 +149,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 const int cand = base + group;
                 const bool valid = cand < n_pop;
                 const Cand k = group_candidate<true>(Pb[cur], a.b, cand, valid, G);
-                double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, nullptr, nullptr, queue,
+                double* A_row = (a.blend && valid) ? a.A_scr + ((size_t)blockIdx.x * n_pop + cand) * a.max_ep : nullptr;
+                double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, A_row, nullptr, queue,
                                                         &s_qcount, a.qcap);
                 for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
                 if (g == 0 && valid) s_chi[cand] = chi;
@@ -144,9 +162,39 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                     const Deferred q = queue[i];
                     const Cand k = candidate<true>(Pb[cur], a.b, q.c);
                     const float4 ep = view.s_ep[q.e];
+                    double* A_rq = a.blend ? a.A_scr + ((size_t)blockIdx.x * n_pop + q.c) * a.max_ep : nullptr;
                     const double term = resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w,
-                                                     nullptr, nullptr, q.e, true);
+                                                     A_rq, nullptr, q.e, true);
                     atomicAdd(&s_chi[q.c], term);
+                }
+                __syncthreads();
+            }
+            if (a.blend) {  // Section 4.2: chi^2 of f A + (1 - f) with f profiled out, per candidate
+                for (int base = 0; base < n_pop; base += per_pass) {
+                    const int cand = base + group;
+                    const double* Ar = a.A_scr + ((size_t)blockIdx.x * n_pop + min(cand, n_pop - 1)) * a.max_ep;
+                    double s_ab = 0.0, s_aa = 0.0;
+                    for (int e = g; cand < n_pop && e < n_ep; e += G) {
+                        double F, w;
+                        staged_fw<MODE>(view, e, F, w);
+                        const double ww = w * w, aa = Ar[e] - 1.0;
+                        s_ab += ww * aa * (F - 1.0);
+                        s_aa += ww * aa * aa;
+                    }
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        s_ab += __shfl_xor_sync(0xffffffffu, s_ab, off);
+                        s_aa += __shfl_xor_sync(0xffffffffu, s_aa, off);
+                    }
+                    const double f = blend_f(s_ab, s_aa, a.f_min);
+                    double chi = 0.0;
+                    for (int e = g; cand < n_pop && e < n_ep; e += G) {
+                        double F, w;
+                        staged_fw<MODE>(view, e, F, w);
+                        const double r = (F - 1.0) - f * (Ar[e] - 1.0);
+                        chi += w * w * r * r;
+                    }
+                    for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
+                    if (g == 0 && cand < n_pop) s_chi[cand] = chi;
                 }
                 __syncthreads();
             }
@@ -245,8 +293,13 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
                     const sblm_bounds* bounds, const sblm_ea_params* params, const sblm_batch_tuning* tuning,
                     const double* seed_genes, int n_seed, double* best_theta, double* best_chi2, Staging& st,
                     int* i_th, int* i_c, Prepared* out, size_t extra_bytes = 0, int* k_extra = nullptr) {
+    if (!params) return fail(SBLM_EINVAL, "params is NULL");
+    const int mode = params->precision & ~SBLM_BLEND;
+    const bool blend = (params->precision & SBLM_BLEND) != 0;
+    sblm_ea_params pm = *params;
+    pm.precision = mode;
     EAConst c;
-    SBLM_TRY(ea_const(params, params ? params->n_pop : 0, SBLM_NPAR, 0, &c));
+    SBLM_TRY(ea_const(&pm, params->n_pop, SBLM_NPAR, 0, &c));
     if (params->n_gen < 1) return fail(SBLM_EINVAL, "n_gen must be >= 1");
     if (n_lc < 1) return fail(SBLM_EINVAL, "n_lc must be >= 1");
     if (!offsets || !best_theta || !best_chi2) return fail(SBLM_EINVAL, "offsets, best_theta and best_chi2 are required");
@@ -268,7 +321,6 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
         max_ep = (int)std::max<int64_t>(max_ep, n);
     }
     const int64_t total = off[n_lc];
-    const int mode = params->precision;
     int G = tuning && tuning->group > 0 ? tuning->group : 16;
     int threads = tuning && tuning->block > 0 ? tuning->block : 512;
     if (G < 1 || G > 32 || (G & (G - 1))) return fail(SBLM_EINVAL, "tuning group must be a power of two <= 32");
@@ -308,7 +360,9 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
     const int k_next = st.scratch(sizeof(unsigned));
     const int k_genes = st.scratch(sizeof(double) * SBLM_NPAR * (size_t)n_lc);
+    const int k_A = st.scratch(blend ? sizeof(double) * (size_t)blocks * c.n_pop * max_ep : 0);
     const int polish_blocks = std::min(n_lc, 2 * sms);
+    const int k_pA = st.scratch(blend && params->polish_fev > 0 ? sizeof(double) * (size_t)polish_blocks * max_ep : 0);
     const unsigned pq = params->polish_fev > 0 ? polish_queue_capacity(mode, max_ep) : 0;
     const int k_pq = st.scratch(deferred_entry_bytes() * (size_t)pq * polish_blocks);
     if (params->polish_fev > 0 && polish_smem_bytes(mode, max_ep) > kPolishSmemBudget)
@@ -353,6 +407,9 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.n_seed = n_seed;
     a.polish_fev = params->polish_fev;
     a.best_genes = static_cast<double*>(st.scratch_ptr(k_genes));
+    a.blend = blend ? 1 : 0;
+    a.f_min = SBLM_BLEND_F_MIN;
+    a.A_scr = blend ? static_cast<double*>(st.scratch_ptr(k_A)) : nullptr;
     out->a = a;
     PolishArgs pa{};
     pa.t = a.t;
@@ -370,6 +427,10 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     pa.maxfev = params->polish_fev;
     pa.queue = static_cast<Deferred*>(st.scratch_ptr(k_pq));
     pa.qcap = pq;
+    pa.blend = blend ? 1 : 0;
+    pa.f_min = SBLM_BLEND_F_MIN;
+    pa.A_scr = blend && params->polish_fev > 0 ? static_cast<double*>(st.scratch_ptr(k_pA)) : nullptr;
+    pa.A_stride = max_ep;
     out->pa = pa;
     out->polish_blocks = polish_blocks;
     out->max_ep = max_ep;

@@ -108,6 +108,8 @@ sblm_status ea_const(const sblm_ea_params* p, int n_pop, int n_par, uint64_t str
     if (!(p->stag_rel >= 0.0) || !std::isfinite(p->stag_rel)) return fail(SBLM_EINVAL, "stag_rel must be >= 0");
     if (p->restart_after < 1) return fail(SBLM_EINVAL, "restart_after must be >= 1");
     if (p->n_tourn < 0) return fail(SBLM_EINVAL, "n_tourn must be >= 0");
+    if (p->precision & SBLM_BLEND)
+        return fail(SBLM_EINVAL, "SBLM_BLEND is taken by sblm_chi2_blend, the batched fitters and sblm_polish_batch");
     if (p->precision < SBLM_FP64 || p->precision > SBLM_FP32) return fail(SBLM_EINVAL, "unknown precision");
     EAConst c;
     c.n_pop = n_pop;

@@ -1,5 +1,5 @@
 // forward.cu -- population-wide forward model: magnification and chi^2 for every
-// (candidate, epoch), sblm_magnification and sblm_chi2.
+// (candidate, epoch): sblm_magnification, sblm_chi2, and the blended chi^2 of sblm_chi2_blend.
 //
 // Layout: G threads per candidate (a power of two, G <= 256), each owning a contiguous run of
 // epochs so that a root set carries over as the warm start of the next epoch; the block's
@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "blend.cuh"
 #include "forward_launch.cuh"
 #include "forward_run.cuh"
 #include "runtime.cuh"
@@ -39,6 +40,39 @@ __global__ void __launch_bounds__(256) resolve_kernel(const double* __restrict__
         const double term = resolve_fp64(q.z, q.why, &k, t[q.e], fe, we, A_out ? A_out + (size_t)q.c * n_ep : nullptr,
                                          flags ? flags + (size_t)q.c * n_ep : nullptr, q.e, CHI2);
         if (CHI2) atomicAdd(&chi2_out[q.c], term);
+    }
+}
+
+// blended chi^2 of candidate (warp) c from its magnification row: lanes take epochs lane,
+// lane + 32, ... in order; the sums meet in a fixed shuffle tree
+__global__ void blend_kernel(const double* __restrict__ A, const double* __restrict__ flux,
+                             const double* __restrict__ sigma, int n_cand, int n_ep, double f_min,
+                             double* __restrict__ chi2_out, double* __restrict__ f_out) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (c >= n_cand) return;  // whole warps leave together
+    const double* Ar = A + (size_t)c * n_ep;
+    double s_ab = 0.0, s_aa = 0.0;
+    for (int e = lane; e < n_ep; e += 32) {
+        const double w = 1.0 / (sigma[e] * sigma[e]);
+        const double a = Ar[e] - 1.0, b = flux[e] - 1.0;
+        s_ab += w * a * b;
+        s_aa += w * a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s_ab += __shfl_xor_sync(0xffffffffu, s_ab, o);
+        s_aa += __shfl_xor_sync(0xffffffffu, s_aa, o);
+    }
+    const double f = blend_f(s_ab, s_aa, f_min);
+    double chi = 0.0;
+    for (int e = lane; e < n_ep; e += 32) {
+        const double w = 1.0 / (sigma[e] * sigma[e]);
+        const double r = (flux[e] - 1.0) - f * (Ar[e] - 1.0);
+        chi += w * r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, o);
+    if (lane == 0) {
+        chi2_out[c] = chi;
+        if (f_out) f_out[c] = f;
     }
 }
 
@@ -289,6 +323,54 @@ extern "C" sblm_status sblm_chi2_genes(const double* P, int32_t n_pop, const sbl
     Bounds b;
     SBLM_TRY(check_bounds(bounds, &b));
     return chi2_impl(P, true, b, n_pop, t, flux, sigma, n_ep, chi2_out, precision, stream);
+}
+
+extern "C" sblm_status sblm_chi2_blend(const double* theta, int32_t n_cand, const double* t, const double* flux,
+                                      const double* sigma, int32_t n_ep, double* chi2_out, double* f_out,
+                                      int32_t precision, void* stream) {
+    if (n_cand < 0 || n_ep < 0) return fail(SBLM_EINVAL, "negative size (n_cand=%d, n_ep=%d)", n_cand, n_ep);
+    if (precision < SBLM_FP64 || precision > SBLM_FP32) return fail(SBLM_EINVAL, "unknown precision %d", precision);
+    if (n_cand == 0) return SBLM_OK;
+    if (!theta || !chi2_out || (n_ep > 0 && (!t || !flux || !sigma))) return fail(SBLM_EINVAL, "NULL buffer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    int i_th, i_t, i_f, i_s, i_c, i_fo;
+    SBLM_TRY(st.arg(theta, sizeof(double) * 6 * (size_t)n_cand, true, false, &i_th));
+    SBLM_TRY(st.arg(t, sizeof(double) * (size_t)n_ep, true, false, &i_t));
+    SBLM_TRY(st.arg(flux, sizeof(double) * (size_t)n_ep, true, false, &i_f));
+    SBLM_TRY(st.arg(sigma, sizeof(double) * (size_t)n_ep, true, false, &i_s));
+    SBLM_TRY(st.arg(chi2_out, sizeof(double) * (size_t)n_cand, false, true, &i_c));
+    SBLM_TRY(st.arg(f_out, f_out ? sizeof(double) * (size_t)n_cand : 0, false, true, &i_fo));
+    const unsigned qcap = precision == SBLM_MIXED ? mixed_queue_capacity(n_cand, n_ep) : 0;
+    const int k_A = st.scratch(sizeof(double) * (size_t)n_cand * n_ep);
+    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
+    bool d = true;
+    SBLM_TRY(is_device_pointer(theta, &d));
+    if (!d) SBLM_TRY(check_theta_host(theta, n_cand));
+    if (n_ep > 0) {
+        SBLM_TRY(is_device_pointer(t, &d));
+        if (!d) SBLM_TRY(check_lightcurve_host(t, flux, sigma, n_ep));
+    }
+    SBLM_TRY(st.begin());
+    ForwardArgs a{};
+    a.src = static_cast<const double*>(st.dev(i_th));
+    a.n_cand = n_cand;
+    a.t = static_cast<const double*>(st.dev(i_t));
+    a.n_ep = n_ep;
+    a.A_out = static_cast<double*>(st.scratch_ptr(k_A));
+    a.mode = precision;
+    a.G = choose_group(n_cand, n_ep);
+    a.queue = st.scratch_ptr(k_q);
+    a.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
+    a.queue_cap = qcap;
+    if (n_ep > 0) SBLM_CUDA(launch_forward(a, s));
+    const int threads = 256, blocks = (int)(((long)n_cand * 32 + threads - 1) / threads);
+    blend_kernel<<<blocks, threads, 0, s>>>(a.A_out, static_cast<const double*>(st.dev(i_f)),
+                                            static_cast<const double*>(st.dev(i_s)), n_cand, n_ep, SBLM_BLEND_F_MIN,
+                                            static_cast<double*>(st.dev(i_c)), static_cast<double*>(st.dev(i_fo)));
+    SBLM_CUDA(cudaGetLastError());
+    return st.end();
 }
 
 extern "C" sblm_status sblm_chi2(const double* theta, int32_t n_cand, const double* t, const double* flux,

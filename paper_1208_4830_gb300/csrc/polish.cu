@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(kPolishThreads) polish_kernel(PolishArgs a) {
         double g[kPolishN];
         for (int j = 0; j < kPolishN; ++j) g[j] = a.g_in[(size_t)lc * a.g_stride + j];
         double f = a.c_in ? a.c_in[(size_t)lc * a.c_stride] : INFINITY;
-        block_nelder_mead<MODE>(g, &f, a.maxfev, a.b, view, n_ep, queue, a.qcap, &s_qcount, s_red);
+        double* A_row = a.blend ? a.A_scr + (size_t)blockIdx.x * a.A_stride : nullptr;
+        block_nelder_mead<MODE>(g, &f, a.maxfev, a.b, view, n_ep, queue, a.qcap, &s_qcount, s_red, A_row, a.f_min);
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int j = 0; j < kPolishN; ++j) a.g_out[(size_t)lc * a.g_stride + j] = g[j];
@@ -99,6 +100,8 @@ extern "C" sblm_status sblm_polish_batch(const double* t, const double* flux, co
                                          double* chi2_out, void* stream) {
     if (n_lc < 1) return fail(SBLM_EINVAL, "n_lc must be >= 1");
     if (maxfev < 0 || maxfev > kPolishMaxFev) return fail(SBLM_EINVAL, "maxfev must be in [0, %d]", kPolishMaxFev);
+    const bool blend = (precision & SBLM_BLEND) != 0;
+    precision &= ~SBLM_BLEND;
     if (precision < SBLM_FP64 || precision > SBLM_FP32) return fail(SBLM_EINVAL, "unknown precision %d", precision);
     if (!t || !flux || !sigma || !offsets || !genes_in || !genes_out || !chi2_out)
         return fail(SBLM_EINVAL, "NULL buffer");
@@ -138,6 +141,7 @@ extern "C" sblm_status sblm_polish_batch(const double* t, const double* flux, co
     SBLM_TRY(st.arg(chi2_out, sizeof(double) * (size_t)n_lc, false, true, &i_c));
     const unsigned qcap = polish_queue_capacity(precision, max_ep);
     const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
+    const int k_A = st.scratch(blend ? sizeof(double) * (size_t)blocks * max_ep : 0);
     bool d1, d2, d3;
     SBLM_TRY(is_device_pointer(t, &d1));
     SBLM_TRY(is_device_pointer(flux, &d2));
@@ -160,6 +164,10 @@ extern "C" sblm_status sblm_polish_batch(const double* t, const double* flux, co
     a.maxfev = maxfev;
     a.queue = static_cast<Deferred*>(st.scratch_ptr(k_q));
     a.qcap = qcap;
+    a.blend = blend ? 1 : 0;
+    a.f_min = SBLM_BLEND_F_MIN;
+    a.A_scr = blend ? static_cast<double*>(st.scratch_ptr(k_A)) : nullptr;
+    a.A_stride = max_ep;
     SBLM_CUDA(launch_polish(precision, a, blocks, max_ep, s));
     return st.end();
 }

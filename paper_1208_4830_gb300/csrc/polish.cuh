@@ -14,6 +14,7 @@
 // `maxfev` objective values have been taken (a step in progress may take up to 6 more).
 #pragma once
 
+#include "blend.cuh"
 #include "forward_run.cuh"
 
 namespace sblm {
@@ -39,10 +40,24 @@ __device__ __forceinline__ double block_sum_bcast(double v, double* s_red) {
     return r;
 }
 
-// chi^2 of the candidate encoded by genes g (identical in every thread), all threads of the block
+// flux and weight 1/sigma of staged epoch e
+template <int MODE>
+__device__ __forceinline__ void polish_fw(const LCView& v, int e, double& F, double& w) {
+    if (MODE == SBLM_FP64) {
+        F = v.s_f[e];
+        w = v.s_w[e];
+    } else {
+        const float4 ep = v.s_ep[e];
+        F = ep.z;
+        w = ep.w;
+    }
+}
+
+// chi^2 of the candidate encoded by genes g (identical in every thread), all threads of the block;
+// with A_row (n_ep doubles of scratch) the chi^2 of the blended model with f profiled out
 template <int MODE>
 __device__ double block_chi2(const double* g, const Bounds& b, const LCView& view, int n_ep, Deferred* queue,
-                             unsigned qcap, unsigned* s_qcount, double* s_red) {
+                             unsigned qcap, unsigned* s_qcount, double* s_red, double* A_row, double f_min) {
     const Cand k = candidate<true>(g, b, 0);
     const int seg = (n_ep + blockDim.x - 1) / blockDim.x;
     const int e0 = min(n_ep, (int)threadIdx.x * seg), e1 = min(n_ep, e0 + seg);
@@ -50,17 +65,39 @@ __device__ double block_chi2(const double* g, const Bounds& b, const LCView& vie
         if (threadIdx.x == 0) *s_qcount = 0;
         __syncthreads();
     }
-    double chi = eval_run<MODE, true, true>(k, true, 0, e0, e1, seg, view, nullptr, nullptr, queue, s_qcount, qcap);
+    double chi = eval_run<MODE, true, true>(k, true, 0, e0, e1, seg, view, A_row, nullptr, queue, s_qcount, qcap);
     if constexpr (MODE == SBLM_MIXED) {
         __syncthreads();
         const unsigned n = min(*s_qcount, qcap);
         for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
             const Deferred q = queue[i];
             const float4 ep = view.s_ep[q.e];
-            chi += resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w, nullptr, nullptr, q.e, true);
+            chi += resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w, A_row, nullptr, q.e, true);
+        }
+    }
+    if (A_row) {  // Section 4.2: f A + (1 - f) with f profiled out
+        __syncthreads();
+        double s_ab = 0.0, s_aa = 0.0;
+        for (int e = threadIdx.x; e < n_ep; e += blockDim.x) {
+            double F, w;
+            polish_fw<MODE>(view, e, F, w);
+            const double ww = w * w, aa = A_row[e] - 1.0;
+            s_ab += ww * aa * (F - 1.0);
+            s_aa += ww * aa * aa;
+        }
+        s_ab = block_sum_bcast(s_ab, s_red);
+        s_aa = block_sum_bcast(s_aa, s_red);
+        const double f = blend_f(s_ab, s_aa, f_min);
+        chi = 0.0;
+        for (int e = threadIdx.x; e < n_ep; e += blockDim.x) {
+            double F, w;
+            polish_fw<MODE>(view, e, F, w);
+            const double r = (F - 1.0) - f * (A_row[e] - 1.0);
+            chi += w * w * r * r;
         }
     }
     const double s = block_sum_bcast(chi, s_red);
+    __syncthreads();  // A_row is rewritten by the next evaluation
     return isfinite(s) ? s : INFINITY;
 }
 
@@ -71,13 +108,13 @@ __device__ __forceinline__ double clamp01(double v) { return fmin(1.0, fmax(0.0,
 template <int MODE>
 __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfev, const Bounds& b, const LCView& view,
                                                int n_ep, Deferred* queue, unsigned qcap, unsigned* s_qcount,
-                                               double* s_red) {
+                                               double* s_red, double* A_row, double f_min) {
     constexpr int n = kPolishN;
     double x[n + 1][n], f[n + 1];
     double xb[n], xr[n], xt[n];
     for (int j = 0; j < n; ++j) x[0][j] = x0[j];
     f[0] = *f0;
-    if (!isfinite(f[0])) f[0] = block_chi2<MODE>(x[0], b, view, n_ep, queue, qcap, s_qcount, s_red);
+    if (!isfinite(f[0])) f[0] = block_chi2<MODE>(x[0], b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
     int fev = 0;
     bool build = true;
     while (fev < maxfev) {
@@ -85,7 +122,7 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
             for (int k = 0; k < n; ++k) {
                 for (int j = 0; j < n; ++j) x[k + 1][j] = x[0][j];
                 x[k + 1][k] = x[0][k] + (x[0][k] + kPolishDelta <= 1.0 ? kPolishDelta : -kPolishDelta);
-                f[k + 1] = block_chi2<MODE>(x[k + 1], b, view, n_ep, queue, qcap, s_qcount, s_red);
+                f[k + 1] = block_chi2<MODE>(x[k + 1], b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
             }
             fev += n;
             build = false;
@@ -116,12 +153,12 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
             xb[j] = __ddiv_rn(s, (double)n);
         }
         for (int j = 0; j < n; ++j) xr[j] = clamp01(__dsub_rn(__dmul_rn(2.0, xb[j]), x[n][j]));
-        const double fr = block_chi2<MODE>(xr, b, view, n_ep, queue, qcap, s_qcount, s_red);
+        const double fr = block_chi2<MODE>(xr, b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
         ++fev;
         bool shrink = false;
         if (fr < f[0]) {  // expansion
             for (int j = 0; j < n; ++j) xt[j] = clamp01(__dsub_rn(__dmul_rn(3.0, xb[j]), __dmul_rn(2.0, x[n][j])));
-            const double fe = block_chi2<MODE>(xt, b, view, n_ep, queue, qcap, s_qcount, s_red);
+            const double fe = block_chi2<MODE>(xt, b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
             ++fev;
             const bool take_e = fe < fr;
             for (int j = 0; j < n; ++j) x[n][j] = take_e ? xt[j] : xr[j];
@@ -135,7 +172,7 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
                 const double to = outside ? xr[j] : x[n][j];
                 xt[j] = clamp01(__dadd_rn(xb[j], __dmul_rn(0.5, __dsub_rn(to, xb[j]))));
             }
-            const double fc = block_chi2<MODE>(xt, b, view, n_ep, queue, qcap, s_qcount, s_red);
+            const double fc = block_chi2<MODE>(xt, b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
             ++fev;
             if (outside ? fc <= fr : fc < f[n]) {
                 for (int j = 0; j < n; ++j) x[n][j] = xt[j];
@@ -147,7 +184,7 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
         if (shrink) {
             for (int k = 1; k <= n; ++k) {
                 for (int j = 0; j < n; ++j) x[k][j] = __dadd_rn(x[0][j], __dmul_rn(0.5, __dsub_rn(x[k][j], x[0][j])));
-                f[k] = block_chi2<MODE>(x[k], b, view, n_ep, queue, qcap, s_qcount, s_red);
+                f[k] = block_chi2<MODE>(x[k], b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
             }
             fev += n;
         }

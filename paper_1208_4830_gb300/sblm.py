@@ -27,6 +27,8 @@ NPAR = 6
 MAX_NPAR = 16
 MAX_WINDOW = 15
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
+BLEND = 16  # OR-ed into a precision: chi^2 of the blended model with f profiled out (Section 4.2)
+BLEND_F_MIN = 1e-3
 STATUS = {0: "SBLM_OK", 1: "SBLM_EINVAL", 2: "SBLM_ENOMEM", 3: "SBLM_ECUDA", 4: "SBLM_ETIMEOUT", 5: "SBLM_ENUMERIC"}
 
 
@@ -92,6 +94,7 @@ _SIGS = {
     "sblm_magnification": (ctypes.c_int, [_p, _i32, _p, _i32, _p, _p, _i32, _p]),
     "sblm_chi2": (ctypes.c_int, [_p, _i32, _p, _p, _p, _i32, _p, _i32, _p]),
     "sblm_chi2_genes": (ctypes.c_int, [_p, _i32, ctypes.POINTER(Bounds), _p, _p, _p, _i32, _p, _i32, _p]),
+    "sblm_chi2_blend": (ctypes.c_int, [_p, _i32, _p, _p, _p, _i32, _p, _p, _i32, _p]),
     "sblm_ea_init": (ctypes.c_int, [_p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _p, _p]),
     "sblm_ea_generation": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_ea_generation_noalloc": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
@@ -154,7 +157,14 @@ def _check(status, where):
 
 
 def _precision(p):
-    return PRECISIONS[p] if isinstance(p, str) else int(p)
+    """An SBLM precision code from "fp64" / "mixed" / "fp32", optionally with "+blend" (the
+    blended-model flag of the batched fitters and the polish), or an int."""
+    if not isinstance(p, str):
+        return int(p)
+    base, _, flag = p.partition("+")
+    if flag not in ("", "blend"):
+        raise ValueError(f"unknown precision flag {flag!r}")
+    return PRECISIONS[base] | (BLEND if flag else 0)
 
 
 def _ptr(x):
@@ -247,6 +257,22 @@ def chi2(theta, t, flux, sigma, precision="fp64", out=None, stream=None):
     st = _lib.sblm_chi2(args[0][0], n_cand, args[1][0], args[2][0], args[3][0], n_ep, args[4][0], _precision(precision), s)
     _check(st, "sblm_chi2")
     return out
+
+
+def chi2_blend(theta, t, flux, sigma, precision="fp64", out=None, f_out=None, stream=None):
+    """(chi^2, f) of each parameter row against the lightcurve for the blended model
+    f A + (1 - f) of Section 4.2 with the blending fraction f profiled out."""
+    n_cand, n_ep = int(theta.shape[0]), int(t.shape[0])
+    if out is None:
+        out = _like(theta, (n_cand,), np.float64)
+    if f_out is None:
+        f_out = _like(theta, (n_cand,), np.float64)
+    args = [_ptr(a) for a in (theta, t, flux, sigma, out, f_out)]
+    s = _stream(stream, theta, t, flux, sigma, out)
+    st = _lib.sblm_chi2_blend(args[0][0], n_cand, args[1][0], args[2][0], args[3][0], n_ep, args[4][0], args[5][0],
+                              _precision(precision), s)
+    _check(st, "sblm_chi2_blend")
+    return out, f_out
 
 
 def chi2_genes(P, t, flux, sigma, lo, hi, precision="fp64", out=None, stream=None):

@@ -258,3 +258,52 @@ def count_peaks(A, rel_prominence=0.01):
             if A[i] - base > rel_prominence * A[i]:
                 n += 1
     return n
+
+
+# Section 2.2's photometric noise model: log10 sigma_I = slope * m_I + intercept (magnitudes)
+NOISE_SLOPE, NOISE_INTERCEPT = 0.3416, -7.7095
+M0_RANGE = (18.0, 22.0)  # Table 1: unlensed magnitude
+
+
+@dataclass
+class NoisyBlendedBatch:
+    t: np.ndarray        # concatenated epochs (sorted within each curve)
+    offsets: np.ndarray  # int64 [n_lc + 1]
+    truth: np.ndarray    # (n_lc, 6) lens and trajectory
+    f: np.ndarray        # (n_lc,) blending fraction: source flux / total unlensed flux
+    m0: np.ndarray       # (n_lc,) baseline magnitude
+    z: np.ndarray        # unit-normal draws, one per epoch
+
+    def observe(self, A_true):
+        """(flux, sigma) normalised to the baseline from the truths' source magnifications
+        (concatenated, any implementation): the true magnitude m = m0 - 2.5 log10(f A + 1 - f)
+        gets Gaussian noise of the noise model's sigma_m(m); the observed flux is
+        10^(-0.4 (m_obs - m0)) and its sigma the first-order image 0.4 ln 10 F sigma_m of the
+        magnitude error at the true flux F."""
+        n = np.diff(self.offsets)
+        f = np.repeat(self.f, n)
+        m0 = np.repeat(self.m0, n)
+        F = f * np.asarray(A_true) + (1.0 - f)
+        m = m0 - 2.5 * np.log10(F)
+        s_m = 10.0 ** (NOISE_SLOPE * m + NOISE_INTERCEPT)
+        flux = 10.0 ** (-0.4 * (m + s_m * self.z - m0))
+        return flux, 0.4 * np.log(10.0) * s_m * F
+
+
+def noisy_blended_batch(n_lc=512, seed=0, n_ep=100):
+    """Curves shaped like the paper's noisy, blended test (Section 4.3): parameters as in
+    paper_batch (Table 1 ranges, q uniform in [0.1, 1]), m0 uniform over Table 1's [18, 22], a
+    blending fraction f uniform on (0, 1], and n_ep epochs drawn uniformly on (t_start, t_end)
+    (sorted), with (t_start - t0)/tE in (-3, -2) and (t_end - t0)/tE in (2, 3)."""
+    g = _rng(seed)
+    u = g.uniform(size=(n_lc, 6))
+    theta = PAPER_LO + (PAPER_HI - PAPER_LO) * u
+    theta[:, 5] = 0.1 + 0.9 * u[:, 5]
+    a = g.uniform(-3.0, -2.0, n_lc)
+    b = g.uniform(2.0, 3.0, n_lc)
+    f = 1.0 - g.uniform(size=n_lc)
+    m0 = g.uniform(*M0_RANGE, size=n_lc)
+    ts = [np.sort(g.uniform(th[0] + ai * th[1], th[0] + bi * th[1], n_ep)) for th, ai, bi in zip(theta, a, b)]
+    z = g.standard_normal(n_lc * n_ep)
+    offsets = np.arange(n_lc + 1, dtype=np.int64) * n_ep
+    return NoisyBlendedBatch(t=np.concatenate(ts), offsets=offsets, truth=theta, f=f, m0=m0, z=z)

@@ -63,3 +63,28 @@ def test_first_step_by_hand():
     np.testing.assert_allclose(seen[3], [0.53, 0.47])
     np.testing.assert_allclose(seen[4], [0.545, 0.44])
     assert math.isclose(f(seen[4]), 0.545 + 0.88)
+
+
+def test_blended_objective_recovers_a_blended_curve():
+    """Section 4.2's blended model: from near the truth of a noise-free curve diluted to f = 0.35,
+    the amoeba on the profiled-f objective returns to the truth (chi^2 ~ 0, f recovered), while
+    the unblended objective is left with a large chi^2."""
+    from oracle import ea
+    from oracle import sblm as osb
+
+    lo = np.array([-20.0, 5.0, 0.0, 0.0, 0.3, -4.0])
+    hi = np.array([20.0, 100.0, 1.0, 2 * np.pi, 3.0, 0.0])
+    truth = np.array([[1.5, 22.0, 0.15, 0.9, 1.2, 0.25]])
+    t = np.linspace(-50.0, 50.0, 120)
+    A = osb.magnification(truth, t)[0]
+    flux = 0.35 * A + 0.65
+    sigma = 0.01 * flux
+    g_true = (np.array([1.5, 22.0, 0.15, 0.9, 1.2, np.log10(0.25)]) - lo) / (hi - lo)
+    start = g_true + np.array([0.004, -0.003, 0.002, 0.001, -0.002, 0.003])
+    g, c, _ = opo.polish_sblm(t, flux, sigma, lo, hi, start, 1500, blend=True)
+    c_start = osb.chi2_blend(ea.sblm_theta(start[None, :], lo, hi), t, flux, sigma)[0][0]
+    assert c < 1e-2 * c_start and c < 1.0
+    _, f = osb.chi2_blend(ea.sblm_theta(np.asarray(g)[None, :], lo, hi), t, flux, sigma)
+    assert f[0] == pytest.approx(0.35, rel=2e-2)
+    _, c_plain, _ = opo.polish_sblm(t, flux, sigma, lo, hi, start, 300)
+    assert c_plain > 100 * max(c, 1.0)

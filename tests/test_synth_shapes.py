@@ -34,3 +34,28 @@ def test_heldout_truths_inside_the_fit_domain():
     g[:, 5] = np.log10(g[:, 5])
     assert np.all((g >= synth.FIT_LO) & (g <= synth.FIT_HI))
     assert b.offsets[-1] == 200 * 50
+
+
+def test_noisy_blended_batch_follows_the_paper_setup():
+    """Section 4.3's changes to the test: random epochs, the noise model of Section 2.2, blending."""
+    b = synth.noisy_blended_batch(50, seed=6)
+    assert b.offsets[-1] == 50 * 100
+    assert np.all((b.f > 0) & (b.f <= 1)) and np.all((b.m0 >= 18) & (b.m0 <= 22))
+    for i in range(50):
+        t = b.t[b.offsets[i] : b.offsets[i + 1]]
+        t0, tE = b.truth[i, 0], b.truth[i, 1]
+        assert np.all(np.diff(t) >= 0) and (t[0] - t0) / tE > -3 and (t[-1] - t0) / tE < 3
+        assert np.std(np.diff(t)) > 0.1 * np.mean(np.diff(t))  # not evenly spaced
+    # at baseline (A = 1) the magnitude error is the noise model's: log10 sigma = 0.3416 m0 - 7.7095
+    flux, sigma = b.observe(np.ones(b.t.size))
+    n = np.diff(b.offsets)
+    m0 = np.repeat(b.m0, n)
+    np.testing.assert_allclose(sigma, 0.4 * np.log(10) * 10 ** (0.3416 * m0 - 7.7095), rtol=1e-12)
+    m_obs = b.m0.repeat(n) - 2.5 * np.log10(flux)
+    r = (m_obs - m0) / 10 ** (0.3416 * m0 - 7.7095)
+    np.testing.assert_allclose(r, b.z, atol=1e-9)
+    # f dilutes the source magnification: F - 1 = f (A - 1) without noise
+    b.z[:] = 0.0
+    A = np.linspace(1.0, 30.0, b.t.size)
+    flux, _ = b.observe(A)
+    np.testing.assert_allclose(flux - 1, np.repeat(b.f, n) * (A - 1), rtol=1e-9, atol=1e-12)
