@@ -268,6 +268,25 @@ sblm_status sblm_autotune_batch(const double* t, const double* flux, const doubl
                                 sblm_batch_tuning* best, double* best_ms, void* stream);
 
 /*
+ * Success monitor of the batched fitter (sblm_fit_batch_monitored): an evaluation instrument for
+ * synthetic lightcurves whose parameters are known. Section 4.2 counts a fitting run as
+ * successful when it returned at least one model with delta chi^2 / nu < 1 and every parameter
+ * within 10% of the injected one, and the EA of Appendix A returns, by default, every population
+ * of every generation. Instead of writing that history out (n_gen x n_pop rows per lightcurve),
+ * the fitter tests each evaluated row as it is produced: chi^2 < chi2_max[l] and every parameter
+ * within rel_tol of theta_ref[l] (t0 relative to the reference tE, alpha as a wrapped difference
+ * relative to 2 pi, tE, u0, d and q relative to their reference values; with SBLM_BLEND and
+ * f_ref given, also the profiled f relative to f_ref[l]). The monitor never steers the search.
+ */
+typedef struct {
+    const double* theta_ref; /* [n_lc * 6] reference parameters (t0, tE, u0, alpha, d, q) */
+    const double* f_ref;     /* [n_lc] reference blending fractions, or NULL */
+    const double* chi2_max;  /* [n_lc] chi^2 bound (strict) */
+    double rel_tol;          /* parameter tolerance, > 0 (0.1 in the paper) */
+    int32_t* first_gen;      /* [n_lc] out: first generation with a matching row, -1 if none */
+} sblm_batch_monitor;
+
+/*
  * chi^2 of the blended model of Section 4.2 (Eq. blend), A_obs = f A + (1 - f), for each
  * parameter row, with the blending fraction profiled out: the paper notes its least-squares value
  * follows from a linear equation. With a_k = A_k - 1, b_k = F_k - 1 and w_k = 1/sigma_k^2,

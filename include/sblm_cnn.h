@@ -167,6 +167,18 @@ sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, const double
                                const float* weights, double seed_frac, double* best_theta,
                                double* best_chi2, void* stream);
 
+/*
+ * sblm_fit_batch_cnn with the success monitor of sblm.h (sblm_batch_monitor; monitor may be
+ * NULL, then this is sblm_fit_batch_cnn). The monitor's arrays follow the pointer rules of the
+ * other arguments (host or device); first_gen is written when the call returns.
+ */
+sblm_status sblm_fit_batch_monitored(const double* t, const double* flux, const double* sigma,
+                                     const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                     const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                     const float* weights, double seed_frac,
+                                     const sblm_batch_monitor* monitor, double* best_theta,
+                                     double* best_chi2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

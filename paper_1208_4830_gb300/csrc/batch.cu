@@ -64,7 +64,34 @@ struct BatchArgs {
     int blend;           // chi^2 of the blended model with f profiled out (Section 4.2)
     double f_min;
     double* A_scr;       // blend: per block n_pop x max_ep magnifications
+    // success monitor (mon_theta nullptr: off)
+    const double* mon_theta;  // [n_lc][6] reference rows
+    const double* mon_f;      // [n_lc] reference blending fractions or nullptr
+    const double* mon_chi2;   // [n_lc] chi^2 bound
+    double mon_tol;
+    int* mon_first;           // [n_lc] first generation with a matching row, -1 if none
+    double* f_scr;            // blend with monitor: per block n_pop profiled f
 };
+
+// Section 4.2's strict test of one evaluated row (genes g) against the reference row: every
+// parameter within tol (t0 relative to the reference tE, alpha as a wrapped difference relative
+// to 2 pi, the others relative to their reference values; f too when f_ref >= 0)
+__device__ __noinline__ bool monitor_match(const double* g, const Bounds& b, const double* ref, double f,
+                                           double f_ref, double tol) {
+    double a[SBLM_NPAR];
+    for (int j = 0; j < SBLM_NPAR; ++j) a[j] = b.lo[j] + (b.hi[j] - b.lo[j]) * g[j];
+    const double two_pi = 6.283185307179586;
+    double da = a[3] - ref[3] + 0.5 * two_pi;
+    da -= two_pi * floor(da / two_pi);
+    bool ok = fabs(a[0] - ref[0]) < tol * fabs(ref[1]);
+    ok &= fabs(a[1] - ref[1]) < tol * fabs(ref[1]);
+    ok &= fabs(a[2] - ref[2]) < tol * fabs(ref[2]);
+    ok &= fabs(da - 0.5 * two_pi) < tol * two_pi;
+    ok &= fabs(a[4] - ref[4]) < tol * fabs(ref[4]);
+    ok &= fabs(exp10(a[5]) - ref[5]) < tol * fabs(ref[5]);
+    if (f_ref >= 0.0) ok &= fabs(f - f_ref) < tol * f_ref;
+    return ok;
+}
 
 // flux and weight 1/sigma of staged epoch e
 template <int MODE>
@@ -97,6 +124,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
     __shared__ int s_job, s_restart;
     __shared__ double s_pmut;
     __shared__ unsigned s_qcount;
+    __shared__ int s_first;
 
     double* P0 = a.P + (size_t)blockIdx.x * 2 * n_pop * n_par;
     double* Pb[2] = {P0, P0 + (size_t)n_pop * n_par};
@@ -133,7 +161,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 for (int e = threadIdx.x; e < a.n_seed * n_par; e += blockDim.x) dst[e] = sg[e];
             }
         }
-        if (threadIdx.x == 0) state_reset(c, s_state);
+        if (threadIdx.x == 0) {
+            state_reset(c, s_state);
+            s_first = -1;
+        }
         __syncthreads();
 
         const int group = threadIdx.x / G, g = threadIdx.x % G;
@@ -194,9 +225,22 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                         chi += w * w * r * r;
                     }
                     for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
-                    if (g == 0 && cand < n_pop) s_chi[cand] = chi;
+                    if (g == 0 && cand < n_pop) {
+                        s_chi[cand] = chi;
+                        if (a.f_scr) a.f_scr[(size_t)blockIdx.x * n_pop + cand] = f;
+                    }
                 }
                 __syncthreads();
+            }
+            if (a.mon_theta) {  // success monitor: every evaluated row against the reference
+                const double bound = a.mon_chi2[lc], f_ref = a.mon_f ? a.mon_f[lc] : -1.0;
+                for (int r = threadIdx.x; r < n_pop; r += blockDim.x) {
+                    if (!(s_chi[r] < bound)) continue;
+                    const double f = a.f_scr ? a.f_scr[(size_t)blockIdx.x * n_pop + r] : 1.0;
+                    if (monitor_match(Pb[cur] + (size_t)r * n_par, a.b, a.mon_theta + (size_t)lc * SBLM_NPAR, f,
+                                      f_ref, a.mon_tol))
+                        atomicCAS(&s_first, -1, gen);
+                }
             }
             // ranking, archive, stagnation
             block_rank(s_chi, n_pop, a.n2, s_key, s_idx);
@@ -234,6 +278,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
             for (int j = 0; j < 5; ++j) th[j] = av[j];
             th[5] = exp10(av[5]);
             a.best_chi2[lc] = s_state.best_chi2;
+            if (a.mon_first) a.mon_first[lc] = s_first;
             for (int j = 0; j < SBLM_NPAR; ++j) a.best_genes[(size_t)lc * SBLM_NPAR + j] = s_state.best_genes[j];
         }
         __syncthreads();
@@ -292,7 +337,8 @@ struct Prepared {
 sblm_status prepare(const double* t, const double* flux, const double* sigma, const int64_t* offsets, int32_t n_lc,
                     const sblm_bounds* bounds, const sblm_ea_params* params, const sblm_batch_tuning* tuning,
                     const double* seed_genes, int n_seed, double* best_theta, double* best_chi2, Staging& st,
-                    int* i_th, int* i_c, Prepared* out, size_t extra_bytes = 0, int* k_extra = nullptr) {
+                    int* i_th, int* i_c, Prepared* out, size_t extra_bytes = 0, int* k_extra = nullptr,
+                    const sblm_batch_monitor* mon = nullptr, int* i_mon = nullptr) {
     if (!params) return fail(SBLM_EINVAL, "params is NULL");
     const int mode = params->precision & ~SBLM_BLEND;
     const bool blend = (params->precision & SBLM_BLEND) != 0;
@@ -375,6 +421,17 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     int i_seed = -1;
     if (seed_genes) SBLM_TRY(st.arg(seed_genes, sizeof(double) * SBLM_NPAR * (size_t)n_lc * n_seed, true, false, &i_seed));
     if (k_extra) *k_extra = st.scratch(extra_bytes);
+    int i_mt = -1, i_mf = -1, i_mc = -1, k_f = -1;
+    if (mon) {
+        if (!mon->theta_ref || !mon->chi2_max || !mon->first_gen)
+            return fail(SBLM_EINVAL, "the monitor needs theta_ref, chi2_max and first_gen");
+        if (!(mon->rel_tol > 0.0) || !std::isfinite(mon->rel_tol)) return fail(SBLM_EINVAL, "monitor rel_tol must be > 0");
+        SBLM_TRY(st.arg(mon->theta_ref, sizeof(double) * SBLM_NPAR * (size_t)n_lc, true, false, &i_mt));
+        SBLM_TRY(st.arg(mon->chi2_max, sizeof(double) * (size_t)n_lc, true, false, &i_mc));
+        if (mon->f_ref) SBLM_TRY(st.arg(mon->f_ref, sizeof(double) * (size_t)n_lc, true, false, &i_mf));
+        SBLM_TRY(st.arg(mon->first_gen, sizeof(int32_t) * (size_t)n_lc, false, true, i_mon));
+        if (blend) k_f = st.scratch(sizeof(double) * (size_t)blocks * c.n_pop);
+    }
     SBLM_TRY(st.begin());
     // longest first (stable): the classic longest-processing-time order for the work queue
     std::vector<int> order(n_lc);
@@ -410,6 +467,14 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.blend = blend ? 1 : 0;
     a.f_min = SBLM_BLEND_F_MIN;
     a.A_scr = blend ? static_cast<double*>(st.scratch_ptr(k_A)) : nullptr;
+    if (mon) {
+        a.mon_theta = static_cast<const double*>(st.dev(i_mt));
+        a.mon_f = i_mf >= 0 ? static_cast<const double*>(st.dev(i_mf)) : nullptr;
+        a.mon_chi2 = static_cast<const double*>(st.dev(i_mc));
+        a.mon_tol = mon->rel_tol;
+        a.mon_first = static_cast<int*>(st.dev(*i_mon));
+        a.f_scr = k_f >= 0 ? static_cast<double*>(st.scratch_ptr(k_f)) : nullptr;
+    }
     out->a = a;
     PolishArgs pa{};
     pa.t = a.t;
@@ -528,32 +593,36 @@ extern "C" sblm_status sblm_fit_batch_tuned(const double* t, const double* flux,
                                  best_chi2, stream);
 }
 
-extern "C" sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, const double* sigma,
-                                          const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
-                                          const sblm_ea_params* params, const sblm_batch_tuning* tuning,
-                                          const float* weights, double seed_frac, double* best_theta,
-                                          double* best_chi2, void* stream) {
+extern "C" sblm_status sblm_fit_batch_monitored(const double* t, const double* flux, const double* sigma,
+                                                const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                                const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                                const float* weights, double seed_frac,
+                                                const sblm_batch_monitor* monitor, double* best_theta,
+                                                double* best_chi2, void* stream) {
     if (!(seed_frac >= 0.0 && seed_frac <= 1.0)) return fail(SBLM_EINVAL, "seed_frac must be in [0, 1]");
     if (!params) return fail(SBLM_EINVAL, "params is NULL");
     const int n_seed = weights ? (int)std::lround(seed_frac * params->n_pop) : 0;
-    if (n_seed == 0)
+    if (n_seed == 0 && !monitor)
         return sblm_fit_batch_seeded(t, flux, sigma, offsets, n_lc, bounds, params, tuning, nullptr, 0, best_theta,
                                      best_chi2, stream);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CallLock lock;
     Staging st(s);
-    int i_th, i_c, k_inf = -1, i_w = -1;
-    SBLM_TRY(st.arg(weights, sizeof(float) * cnn::kNParams, true, false, &i_w));
+    int i_th, i_c, k_inf = -1, i_w = -1, i_mon = -1;
+    if (n_seed > 0) SBLM_TRY(st.arg(weights, sizeof(float) * cnn::kNParams, true, false, &i_w));
     Prepared p;
     SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, nullptr, n_seed, best_theta, best_chi2, st,
-                     &i_th, &i_c, &p, cnn::infer_scratch_bytes(n_lc, n_seed), &k_inf));
-    const cnn::InferScratch sc = cnn::infer_scratch_carve(st.scratch_ptr(k_inf), n_lc, n_seed);
-    SBLM_CUDA(cnn::launch_seed_rows(p.a.t, p.a.flux, p.a.sigma, p.a.offsets, n_lc,
-                                    static_cast<const float*>(st.dev(i_w)), p.a.b, n_seed, params->seed, sc, s));
-    p.a.prop_out = sc.out;
-    p.a.prop_win = sc.window;
-    p.a.prop_seed = params->seed;
-    SBLM_TRY(cnn::check_timeout(s));
+                     &i_th, &i_c, &p, n_seed > 0 ? cnn::infer_scratch_bytes(n_lc, n_seed) : 0,
+                     n_seed > 0 ? &k_inf : nullptr, monitor, &i_mon));
+    if (n_seed > 0) {
+        const cnn::InferScratch sc = cnn::infer_scratch_carve(st.scratch_ptr(k_inf), n_lc, n_seed);
+        SBLM_CUDA(cnn::launch_seed_rows(p.a.t, p.a.flux, p.a.sigma, p.a.offsets, n_lc,
+                                        static_cast<const float*>(st.dev(i_w)), p.a.b, n_seed, params->seed, sc, s));
+        p.a.prop_out = sc.out;
+        p.a.prop_win = sc.window;
+        p.a.prop_seed = params->seed;
+        SBLM_TRY(cnn::check_timeout(s));
+    }
     SBLM_TRY(run_graph(p, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));
@@ -607,4 +676,13 @@ extern "C" sblm_status sblm_autotune_batch(const double* t, const double* flux, 
     *best = best_cfg;
     if (best_ms) *best_ms = best_t;
     return SBLM_OK;
+}
+
+extern "C" sblm_status sblm_fit_batch_cnn(const double* t, const double* flux, const double* sigma,
+                                          const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                          const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                          const float* weights, double seed_frac, double* best_theta,
+                                          double* best_chi2, void* stream) {
+    return sblm_fit_batch_monitored(t, flux, sigma, offsets, n_lc, bounds, params, tuning, weights, seed_frac, nullptr,
+                                    best_theta, best_chi2, stream);
 }

@@ -68,6 +68,16 @@ class BatchTuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("block", ctypes.c_int32)]
 
 
+class BatchMonitor(ctypes.Structure):
+    _fields_ = [
+        ("theta_ref", ctypes.c_void_p),
+        ("f_ref", ctypes.c_void_p),
+        ("chi2_max", ctypes.c_void_p),
+        ("rel_tol", ctypes.c_double),
+        ("first_gen", ctypes.c_void_p),
+    ]
+
+
 class CnnTrainParams(ctypes.Structure):
     _fields_ = [
         ("batch", ctypes.c_int32),
@@ -122,6 +132,11 @@ _SIGS = {
         ctypes.c_int,
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p,
          ctypes.c_double, _p, _p, _p],
+    ),
+    "sblm_fit_batch_monitored": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p,
+         ctypes.c_double, ctypes.POINTER(BatchMonitor), _p, _p, _p],
     ),
     "sblm_polish_batch": (
         ctypes.c_int,
@@ -477,6 +492,32 @@ def fit_batch_cnn(t, flux, sigma, offsets, lo, hi, p, weights, seed_frac=0.5, tu
                                  a[4][0], float(seed_frac), best.ctypes.data, best_chi2.ctypes.data, s)
     _check(st, "sblm_fit_batch_cnn")
     return best, best_chi2
+
+
+def fit_batch_monitored(t, flux, sigma, offsets, lo, hi, p, theta_ref, chi2_max, f_ref=None, rel_tol=0.1,
+                        weights=None, seed_frac=0.5, tuning=None, stream=None):
+    """fit_batch_cnn plus the success monitor: (best theta, chi^2, first generation at which some
+    evaluated row had chi^2 < chi2_max and every parameter within rel_tol of theta_ref, -1 if
+    none) per lightcurve."""
+    n_lc = int(offsets.shape[0]) - 1
+    b = bounds(lo, hi)
+    best = np.empty((n_lc, 6))
+    best_chi2 = np.empty(n_lc)
+    first = np.empty(n_lc, dtype=np.int32)
+    ref = np.ascontiguousarray(theta_ref, dtype=np.float64)
+    cmax = np.ascontiguousarray(chi2_max, dtype=np.float64)
+    fr = None if f_ref is None else np.ascontiguousarray(f_ref, dtype=np.float64)
+    mon = BatchMonitor(ref.ctypes.data, None if fr is None else fr.ctypes.data, cmax.ctypes.data, float(rel_tol),
+                       first.ctypes.data)
+    tuning = _tuning(tuning, t, flux, sigma, offsets, lo, hi, p, stream)
+    a = [_ptr(x) for x in (t, flux, sigma, offsets, weights)]
+    s = _stream(stream, t, flux, sigma, weights)
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    st = _lib.sblm_fit_batch_monitored(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p),
+                                       tp, a[4][0], float(seed_frac), ctypes.byref(mon), best.ctypes.data,
+                                       best_chi2.ctypes.data, s)
+    _check(st, "sblm_fit_batch_monitored")
+    return best, best_chi2, first
 
 
 # ------------------------------------------------------------------------------------------
