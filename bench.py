@@ -265,6 +265,7 @@ def make_device_step(sblm, P_in, t, flux, sigma, precision, dev):
 FIT_LCS, FIT_LCS_FP64, FIT_EP, FIT_POP, FIT_GEN, FIT_POLISH = 256, 152, 500, 1024, 150, 2000
 # a smaller budget at which the two MIXED arms are also compared (the proposal's gain shows there)
 FIT_POP_SMALL, FIT_GEN_SMALL = 512, 150
+ISLAND_MIGRATION = 20
 PROPOSAL_STEPS, PROPOSAL_BATCH = 1024, 1024  # 1,048,576 training curves
 SEED_FRAC = 0.5
 # algorithmic flop of one training sample: forward products 2 K N per output position, backward
@@ -328,10 +329,11 @@ def run_fits(sblm, args):
         "flop_per_sample": CNN_STEP_FLOP_PER_SAMPLE,
     }
 
-    def arm(precision, frac, n_lc, n_pop=FIT_POP, n_gen=FIT_GEN):
+    def arm(precision, frac, n_lc, n_pop=FIT_POP, n_gen=FIT_GEN, n_isl=1):
         d = dev if n_lc == FIT_LCS else [torch.tensor(x, device="cuda") for x in (
             b.t[: b.offsets[n_lc]], flux[: b.offsets[n_lc]], sigma[: b.offsets[n_lc]], b.offsets[: n_lc + 1])]
-        p = sblm.params(n_pop=n_pop, n_gen=n_gen, precision=precision, seed=1, polish_fev=FIT_POLISH)
+        p = sblm.params(n_pop=n_pop, n_gen=n_gen, precision=precision, seed=1, polish_fev=FIT_POLISH,
+                        n_islands=n_isl, migration_interval=ISLAND_MIGRATION)
         if precision != "fp64":  # graph capture outside the timed call (FP64 is timed once, cold graph)
             sblm.fit_batch_cnn(*d, synth.FIT_LO, synth.FIT_HI, p, w, seed_frac=frac)
         torch.cuda.synchronize()
@@ -340,8 +342,9 @@ def run_fits(sblm, args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         return {"fits_per_s": n_lc / dt, "seconds": dt, "n_lightcurves": n_lc, "n_pop": n_pop, "n_gen": n_gen,
+                "n_islands": n_isl,
                 "success": _success(best, chi, chi_true[:n_lc], b.truth[:n_lc], FIT_EP),
-                "magnifications_per_s": n_pop * n_gen * FIT_EP * n_lc / dt}
+                "magnifications_per_s": n_isl * n_pop * n_gen * FIT_EP * n_lc / dt}
 
     out = {"workload": f"held-out synthetic curves (sweep priors, 10% through caustics), {FIT_EP} epochs, "
                        f"2% noise; N_pop {FIT_POP} x {FIT_GEN} generations + amoeba polish ({FIT_POLISH} "
@@ -353,6 +356,9 @@ def run_fits(sblm, args):
     out["plain_fp64"] = arm("fp64", 0.0, FIT_LCS_FP64)
     out["smaller_budget"] = {"seeded_mixed": arm("mixed", SEED_FRAC, FIT_LCS, FIT_POP_SMALL, FIT_GEN_SMALL),
                              "plain_mixed": arm("mixed", 0.0, FIT_LCS, FIT_POP_SMALL, FIT_GEN_SMALL)}
+    # the island EA of Section 5.3 at the main arms' budget: 4 populations of N_pop / 4 with a ring
+    # migration of their elites every ISLAND_MIGRATION generations
+    out["islands_mixed"] = arm("mixed", 0.0, FIT_LCS, FIT_POP // 4, FIT_GEN, n_isl=4)
     out["fits_per_s_seeded_mixed_over_plain_fp64"] = out["seeded_mixed"]["fits_per_s"] / out["plain_fp64"]["fits_per_s"]
     out["paper_workload"] = run_paper_workload(sblm, w)
     out["paper_noisy_blended_workload"] = run_noisy_blended_workload(sblm, w)

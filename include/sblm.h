@@ -90,6 +90,13 @@ typedef struct {
                               downhill-simplex search in the genes (sblm_fit, sblm_fit_batch*);
                               0 = the EA alone (default) */
     uint64_t seed;         /* Philox4x64-10 key word 0; key word 1 is the population's stream id */
+    int32_t n_islands;     /* island EA of Section 5.3 (batched fitters only): populations per
+                              lightcurve, each of n_pop rows, evolved side by side; <= 1 = one
+                              population (the paper's experiments, default). Island i of
+                              lightcurve l draws on stream id l + i * n_lc. */
+    int32_t migration_interval; /* with islands: every this many generations the elite of island i
+                              replaces the last row of island (i + 1) mod n_islands (a ring);
+                              <= 0 = islands never exchange rows (independent restarts) */
 } sblm_ea_params;
 
 /* Dynamic state of one population between generations (Appendix A, "Stagnation checks"). */
@@ -111,7 +118,8 @@ const char* sblm_status_str(sblm_status s);
 const char* sblm_last_error(void);
 
 /* Fill *p with the paper's defaults: N_pop 1000, N_gen 100, p_mut0 0.01, N_tourn ceil(N_pop/25),
- * window 10, 1%, restart after 10, SBLM_MIXED, seed 0. */
+ * window 10, 1%, restart after 10, SBLM_MIXED, seed 0; one population (n_islands 1, migration
+ * interval 20 if islands are asked for). */
 void sblm_ea_params_default(sblm_ea_params* p);
 
 /*

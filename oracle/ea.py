@@ -38,6 +38,9 @@ Readings where the paper is silent or loose:
   population is then re-initialised with the generation counter t + 1, p_mut returns to its
   starting value, the window is cleared; the best solution ever seen is archived throughout.
 
+Section 5.3's island EA (``run_islands``, ``migrate_ring``) is this sequence on several
+populations with a ring migration of their elites.
+
 Pinned by tests/test_oracle_ea.py: Philox streams, the closed-form tournament rank CDF
 1 - (1 - r/N)^k, the log-uniform creep step, binomial jump counts, the antithetic pairing of the
 initial population, the convex-combination invariants of the three reproduction modes, scripted
@@ -282,6 +285,48 @@ def run(fitness, n_par, params, trace=None):
         else:
             P = generation(P, chi2, state, params, g)
     return state
+
+
+# ---------------------------------------------------------------------------------------------
+# Section 5.3, "island" EAs: several populations evolve side by side with periodic migration
+# ---------------------------------------------------------------------------------------------
+def migrate_ring(P_next, elites):
+    """One migration step: the elite of island i (its best row of the generation just ranked)
+    replaces the last row of island (i + 1) mod n of the next populations. The paper names the
+    scheme without its settings; the ring, one migrant and the last row are this build's reading."""
+    n = len(P_next)
+    out = [P.copy() for P in P_next]
+    for i in range(n):
+        out[(i + 1) % n][-1] = elites[i]
+    return out
+
+
+def run_islands(fitness, n_par, params, n_islands, interval, n_lc=1):
+    """Island EA: population i uses stream id params.stream + i * n_lc; each generation every
+    island is evaluated and advanced by ``generation``; when (g + 1) is a multiple of
+    ``interval`` (> 0) the elites migrate by ``migrate_ring``. Returns the island states; the
+    run's best is the lowest best_chi2 (the lowest island on ties)."""
+    isl = []
+    for i in range(n_islands):
+        p = EAParams(**{**params.__dict__, "stream": params.stream + i * n_lc})
+        isl.append([p, new_state(p), init_population(p.n_pop, n_par, p, 0)])
+    for g in range(params.n_gen):
+        last = g == params.n_gen - 1
+        nexts, elites = [], []
+        for p, state, P in isl:
+            chi2 = np.asarray(fitness(P), dtype=np.float64)
+            Pr, cr, _ = rank(P, chi2)
+            elites.append(Pr[0].copy())
+            if last:
+                archive(state, Pr, cr)
+                nexts.append(P)
+            else:
+                nexts.append(generation(P, chi2, state, p, g))
+        if not last and interval > 0 and (g + 1) % interval == 0:
+            nexts = migrate_ring(nexts, elites)
+        for k, P in enumerate(nexts):
+            isl[k][2] = P
+    return [state for _, state, _ in isl]
 
 
 def fit_sblm(t, flux, sigma, lo, hi, params, trace=None):

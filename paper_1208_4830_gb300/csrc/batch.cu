@@ -32,6 +32,7 @@ sblm_status check_bounds(const sblm_bounds* b, Bounds* out);
 namespace {
 
 constexpr int kBatchMaxThreads = 512;
+constexpr int kMaxIslands = 64;
 constexpr size_t kBatchSmemBudget = 200 * 1024;  // dynamic shared memory per block
 
 struct BatchArgs {
@@ -64,6 +65,10 @@ struct BatchArgs {
     int blend;           // chi^2 of the blended model with f profiled out (Section 4.2)
     double f_min;
     double* A_scr;       // blend: per block n_pop x max_ep magnifications
+    int n_isl;           // island EA (Section 5.3): populations per lightcurve (1: the paper's panmictic EA)
+    int mig_every;       // ring migration of the islands' elites every this many generations (0: never)
+    sblm_ea_state* isl_state;  // n_isl > 1: per block n_isl states between generations
+    double* isl_elite;         // n_isl > 1: per block n_isl x 6 genes of each island's last elite
     // success monitor (mon_theta nullptr: off)
     const double* mon_theta;  // [n_lc][6] reference rows
     const double* mon_f;      // [n_lc] reference blending fractions or nullptr
@@ -126,11 +131,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
     __shared__ unsigned s_qcount;
     __shared__ int s_first;
 
-    double* P0 = a.P + (size_t)blockIdx.x * 2 * n_pop * n_par;
-    double* Pb[2] = {P0, P0 + (size_t)n_pop * n_par};
+    const int n_isl = a.n_isl;
     uint64_t* keys = a.keys + (size_t)blockIdx.x * n_pop * n_par;
     Deferred* queue = a.queue + (size_t)blockIdx.x * a.qcap;
     const int m = n_pop * n_par;
+    double* const Pi = a.P + (size_t)blockIdx.x * n_isl * 2 * m;  // island i: rows Pi + i 2m (two buffers)
+    sblm_ea_state* const st_g = a.isl_state + (size_t)blockIdx.x * n_isl;
+    double* const elite = a.isl_elite + (size_t)blockIdx.x * n_isl * n_par;
 
     for (;;) {
         if (threadIdx.x == 0) s_job = (int)atomicAdd(a.next, 1u);
@@ -143,28 +150,34 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
         const int n_ep = (int)(a.offsets[lc + 1] - e_begin);
         const LCView view = stage_lightcurve<MODE, true>(smem, a.t + e_begin, a.flux + e_begin, a.sigma + e_begin, n_ep);
         EAConst c = a.c;
-        c.stream = (uint64_t)lc;
 
-        // Appendix A, "Initialisation"
-        for (int e = threadIdx.x; e < m; e += blockDim.x) keys[e] = init_key(c, 0, (uint64_t)e);
-        __syncthreads();
-        block_init_values(c, 0, keys, m, Pb[0], 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key), a.n2);
-        if (a.n_seed > 0) {  // proposal rows replace the last n_seed random rows
+        // Appendix A, "Initialisation", of every island (island i: stream id lc + i n_lc); the
+        // proposal rows replace the last n_seed random rows of island 0
+        for (int isl = 0; isl < n_isl; ++isl) {
+            c.stream = (uint64_t)lc + (uint64_t)isl * a.n_lc;
+            double* const P0 = Pi + (size_t)isl * 2 * m;
+            for (int e = threadIdx.x; e < m; e += blockDim.x) keys[e] = init_key(c, 0, (uint64_t)e);
             __syncthreads();
-            double* dst = Pb[0] + (size_t)(n_pop - a.n_seed) * n_par;
-            if (a.prop_out) {
-                for (int r = threadIdx.x; r < a.n_seed; r += blockDim.x)
-                    proposal_row(a.prop_out + 12 * (size_t)lc, a.prop_win[2 * lc], a.prop_win[2 * lc + 1], a.b,
-                                 a.prop_seed, (uint64_t)lc, (uint64_t)r, 0, dst + (size_t)r * n_par);
-            } else {
-                const double* sg = a.seed + (size_t)lc * a.n_seed * n_par;
-                for (int e = threadIdx.x; e < a.n_seed * n_par; e += blockDim.x) dst[e] = sg[e];
+            block_init_values(c, 0, keys, m, P0, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key), a.n2);
+            if (isl == 0 && a.n_seed > 0) {
+                __syncthreads();
+                double* dst = P0 + (size_t)(n_pop - a.n_seed) * n_par;
+                if (a.prop_out) {
+                    for (int r = threadIdx.x; r < a.n_seed; r += blockDim.x)
+                        proposal_row(a.prop_out + 12 * (size_t)lc, a.prop_win[2 * lc], a.prop_win[2 * lc + 1], a.b,
+                                     a.prop_seed, (uint64_t)lc, (uint64_t)r, 0, dst + (size_t)r * n_par);
+                } else {
+                    const double* sg = a.seed + (size_t)lc * a.n_seed * n_par;
+                    for (int e = threadIdx.x; e < a.n_seed * n_par; e += blockDim.x) dst[e] = sg[e];
+                }
             }
+            if (threadIdx.x == 0) {
+                state_reset(c, s_state);
+                if (n_isl > 1) st_g[isl] = s_state;
+            }
+            __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            state_reset(c, s_state);
-            s_first = -1;
-        }
+        if (threadIdx.x == 0) s_first = -1;
         __syncthreads();
 
         const int group = threadIdx.x / G, g = threadIdx.x % G;
@@ -173,13 +186,21 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
         const int e0 = min(n_ep, g * seg), e1 = min(n_ep, e0 + seg);
         int cur = 0;
         for (int gen = 0; gen < a.n_gen; ++gen) {
+          const bool produce = gen + 1 < a.n_gen;
+          for (int isl = 0; isl < n_isl; ++isl) {
+            c.stream = (uint64_t)lc + (uint64_t)isl * a.n_lc;
+            double* const Pc = Pi + (size_t)isl * 2 * m + (size_t)cur * m;
+            double* const Pn = Pi + (size_t)isl * 2 * m + (size_t)(cur ^ 1) * m;
             // fitness of every row (decode + forward model + chi^2)
-            if (threadIdx.x == 0) s_qcount = 0;
+            if (threadIdx.x == 0) {
+                s_qcount = 0;
+                if (n_isl > 1) s_state = st_g[isl];
+            }
             __syncthreads();
             for (int base = 0; base < n_pop; base += per_pass) {
                 const int cand = base + group;
                 const bool valid = cand < n_pop;
-                const Cand k = group_candidate<true>(Pb[cur], a.b, cand, valid, G);
+                const Cand k = group_candidate<true>(Pc, a.b, cand, valid, G);
                 double* A_row = (a.blend && valid) ? a.A_scr + ((size_t)blockIdx.x * n_pop + cand) * a.max_ep : nullptr;
                 double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, A_row, nullptr, queue,
                                                         &s_qcount, a.qcap);
@@ -191,7 +212,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 const unsigned n = min(s_qcount, a.qcap);
                 for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
                     const Deferred q = queue[i];
-                    const Cand k = candidate<true>(Pb[cur], a.b, q.c);
+                    const Cand k = candidate<true>(Pc, a.b, q.c);
                     const float4 ep = view.s_ep[q.e];
                     double* A_rq = a.blend ? a.A_scr + ((size_t)blockIdx.x * n_pop + q.c) * a.max_ep : nullptr;
                     const double term = resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w,
@@ -237,41 +258,62 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 for (int r = threadIdx.x; r < n_pop; r += blockDim.x) {
                     if (!(s_chi[r] < bound)) continue;
                     const double f = a.f_scr ? a.f_scr[(size_t)blockIdx.x * n_pop + r] : 1.0;
-                    if (monitor_match(Pb[cur] + (size_t)r * n_par, a.b, a.mon_theta + (size_t)lc * SBLM_NPAR, f,
+                    if (monitor_match(Pc + (size_t)r * n_par, a.b, a.mon_theta + (size_t)lc * SBLM_NPAR, f,
                                       f_ref, a.mon_tol))
                         atomicCAS(&s_first, -1, gen);
                 }
             }
             // ranking, archive, stagnation
             block_rank(s_chi, n_pop, a.n2, s_key, s_idx);
-            const bool produce = gen + 1 < a.n_gen;
             if (threadIdx.x == 0) {
                 double p_used = 0.0;
-                s_restart = block_bookkeeping(c, gen, s_key[0], Pb[cur] + (size_t)s_idx[0] * n_par, s_state,
-                                              produce, &p_used);
+                s_restart = block_bookkeeping(c, gen, s_key[0], Pc + (size_t)s_idx[0] * n_par, s_state, produce,
+                                              &p_used);
                 s_pmut = p_used;
-            }
-            __syncthreads();
-            if (!produce) break;
-            double* next = Pb[cur ^ 1];
-            if (s_restart) {
-                for (int e = threadIdx.x; e < m; e += blockDim.x)
-                    keys[e] = init_key(c, (uint64_t)(gen + 1), (uint64_t)e);
-                __syncthreads();
-                block_init_values(c, gen + 1, keys, m, next, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
-                                  a.n2);
-            } else {
-                if (threadIdx.x == 0) {
-                    const double* e = Pb[cur] + (size_t)s_idx[0] * n_par;
-                    for (int j = 0; j < n_par; ++j) next[j] = e[j];
+                if (n_isl > 1) {
+                    st_g[isl] = s_state;
+                    for (int j = 0; j < n_par; ++j) elite[isl * n_par + j] = Pc[(size_t)s_idx[0] * n_par + j];
                 }
-                for (int k = threadIdx.x; k < n_pop / 2; k += blockDim.x)
-                    offspring_pair(c, gen, Pb[cur], s_idx, s_pmut, k, next);
             }
             __syncthreads();
+            if (produce) {
+                if (s_restart) {
+                    for (int e = threadIdx.x; e < m; e += blockDim.x)
+                        keys[e] = init_key(c, (uint64_t)(gen + 1), (uint64_t)e);
+                    __syncthreads();
+                    block_init_values(c, gen + 1, keys, m, Pn, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
+                                      a.n2);
+                } else {
+                    if (threadIdx.x == 0) {
+                        const double* e = Pc + (size_t)s_idx[0] * n_par;
+                        for (int j = 0; j < n_par; ++j) Pn[j] = e[j];
+                    }
+                    for (int k = threadIdx.x; k < n_pop / 2; k += blockDim.x)
+                        offspring_pair(c, gen, Pc, s_idx, s_pmut, k, Pn);
+                }
+                __syncthreads();
+            }
+          }
+            if (!produce) break;
+            if (n_isl > 1 && a.mig_every > 0 && (gen + 1) % a.mig_every == 0) {
+                // Section 5.3, island EA: the elite of island i replaces the last row of the next
+                // population of island (i + 1) mod n_isl
+                for (int e = threadIdx.x; e < n_isl * n_par; e += blockDim.x) {
+                    const int from = e / n_par, j = e % n_par, to = (from + 1) % n_isl;
+                    Pi[(size_t)to * 2 * m + (size_t)(cur ^ 1) * m + (size_t)(n_pop - 1) * n_par + j] =
+                        elite[from * n_par + j];
+                }
+                __syncthreads();
+            }
             cur ^= 1;
         }
         if (threadIdx.x == 0) {
+            if (n_isl > 1) {  // the lightcurve's best over its islands (the lowest island on ties)
+                int bi = 0;
+                for (int i = 1; i < n_isl; ++i)
+                    if (st_g[i].best_chi2 < st_g[bi].best_chi2) bi = i;
+                s_state = st_g[bi];
+            }
             double av[SBLM_NPAR];
             for (int j = 0; j < SBLM_NPAR; ++j) av[j] = a.b.lo[j] + (a.b.hi[j] - a.b.lo[j]) * s_state.best_genes[j];
             double* th = a.best_theta + (size_t)lc * SBLM_NPAR;
@@ -401,7 +443,11 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     const unsigned qcap =
         mode == SBLM_MIXED ? (unsigned)std::min<long>(std::max<long>((long)c.n_pop * max_ep / 4, 4096), 65536) : 0;
     const int k_order = st.scratch(sizeof(int) * n_lc);
-    const int k_P = st.scratch(sizeof(double) * 2 * (size_t)c.n_pop * SBLM_NPAR * blocks);
+    const int n_isl = std::max(1, params->n_islands);
+    if (n_isl > kMaxIslands) return fail(SBLM_EINVAL, "n_islands=%d outside [1, %d]", n_isl, kMaxIslands);
+    const int k_P = st.scratch(sizeof(double) * 2 * (size_t)c.n_pop * SBLM_NPAR * blocks * n_isl);
+    const int k_is = st.scratch(n_isl > 1 ? sizeof(sblm_ea_state) * (size_t)blocks * n_isl : 0);
+    const int k_ie = st.scratch(n_isl > 1 ? sizeof(double) * SBLM_NPAR * (size_t)blocks * n_isl : 0);
     const int k_keys = st.scratch(sizeof(uint64_t) * (size_t)c.n_pop * SBLM_NPAR * blocks);
     const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
     const int k_next = st.scratch(sizeof(unsigned));
@@ -467,6 +513,10 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.blend = blend ? 1 : 0;
     a.f_min = SBLM_BLEND_F_MIN;
     a.A_scr = blend ? static_cast<double*>(st.scratch_ptr(k_A)) : nullptr;
+    a.n_isl = n_isl;
+    a.mig_every = std::max(0, params->migration_interval);
+    a.isl_state = n_isl > 1 ? static_cast<sblm_ea_state*>(st.scratch_ptr(k_is)) : nullptr;
+    a.isl_elite = n_isl > 1 ? static_cast<double*>(st.scratch_ptr(k_ie)) : nullptr;
     if (mon) {
         a.mon_theta = static_cast<const double*>(st.dev(i_mt));
         a.mon_f = i_mf >= 0 ? static_cast<const double*>(st.dev(i_mf)) : nullptr;

@@ -73,6 +73,7 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     EAConst c;
     SBLM_TRY(ea_const(params, params ? params->n_pop : 0, SBLM_NPAR, 0, &c));
     if (params->n_gen < 1) return fail(SBLM_EINVAL, "n_gen must be >= 1");
+    if (params->n_islands > 1) return fail(SBLM_EINVAL, "islands are run by the batched fitters (sblm_fit_batch*)");
     if (n_ep < 1) return fail(SBLM_EINVAL, "n_ep must be >= 1");
     if (!best_theta || !best_chi2) return fail(SBLM_EINVAL, "best_theta and best_chi2 are required");
     Bounds b;

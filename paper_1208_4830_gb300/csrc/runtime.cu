@@ -228,6 +228,8 @@ void sblm_ea_params_default(sblm_ea_params* p) {
     p->precision = SBLM_MIXED;
     p->polish_fev = 0;
     p->seed = 0;
+    p->n_islands = 1;
+    p->migration_interval = 20;
 }
 
 }  // extern "C"

@@ -48,6 +48,8 @@ class EAParams(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("polish_fev", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
+        ("n_islands", ctypes.c_int32),
+        ("migration_interval", ctypes.c_int32),
     ]
 
 

@@ -180,3 +180,54 @@ def test_sblm_decoding():
     assert np.allclose(th[0], [-20, 5, 0, 0, 0.3, 1e-4])
     assert np.allclose(th[1], [20, 100, 1, 2 * np.pi, 3, 1.0])
     assert np.allclose(th[2], [0, 52.5, 0.5, np.pi, 1.65, 1e-2])
+
+
+def test_one_island_is_the_panmictic_ea():
+    f = lambda P: ((P - 0.3) ** 2).sum(1)  # noqa: E731
+    p = params(n_pop=24, n_gen=40, seed=2, stream=5)
+    st = ea.run(f, 4, p)
+    (si,) = ea.run_islands(f, 4, p, 1, 7)
+    assert si.best_chi2 == st.best_chi2 and np.array_equal(si.best_genes, st.best_genes)
+
+
+def test_islands_without_migration_are_independent_runs():
+    f = lambda P: np.abs(np.sin(9 * P)).sum(1)  # noqa: E731
+    p = params(n_pop=20, n_gen=30, seed=3, stream=2)
+    states = ea.run_islands(f, 3, p, 3, 0, n_lc=10)
+    for i, s in enumerate(states):
+        ref = ea.run(f, 3, params(n_pop=20, n_gen=30, seed=3, stream=2 + 10 * i))
+        assert s.best_chi2 == ref.best_chi2 and np.array_equal(s.best_genes, ref.best_genes)
+
+
+def test_ring_migration_by_hand():
+    P = [np.full((3, 2), float(k)) for k in range(3)]
+    elites = [np.array([10.0 * k, 10.0 * k + 1]) for k in range(3)]
+    out = ea.migrate_ring(P, elites)
+    for k in range(3):
+        src = (k - 1) % 3
+        assert np.array_equal(out[k][-1], elites[src])  # last row from the previous island
+        assert np.array_equal(out[k][:-1], P[k][:-1])  # the rest untouched
+        assert np.array_equal(P[k], np.full((3, 2), float(k)))  # inputs not modified
+
+
+def test_migrants_reach_the_neighbour():
+    """Island 1 optimises a far target; island 0's fitness is the same function, but island 0
+    starts far away. After a migration the neighbour evaluates the migrant, so every island's
+    archive is at least as good as the best elite it was sent."""
+    target = np.array([0.9, 0.1, 0.8])
+    calls = []
+
+    def f(P):
+        calls.append(P.copy())
+        return ((P - target) ** 2).sum(1)
+
+    p = params(n_pop=16, n_gen=25, seed=4)
+    states = ea.run_islands(f, 3, p, 3, 5)
+    # populations are evaluated island by island, generation by generation
+    pops = [calls[g * 3 : g * 3 + 3] for g in range(25)]
+    for g in range(4, 24, 5):  # migrations after generations 4, 9, 14, 19
+        for i in range(3):
+            chi = ((pops[g][i] - target) ** 2).sum(1)
+            elite = pops[g][i][int(np.argmin(chi))]
+            assert np.array_equal(pops[g + 1][(i + 1) % 3][-1], elite)
+            assert states[(i + 1) % 3].best_chi2 <= chi.min()
