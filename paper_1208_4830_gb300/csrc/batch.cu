@@ -186,114 +186,115 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
         const int e0 = min(n_ep, g * seg), e1 = min(n_ep, e0 + seg);
         int cur = 0;
         for (int gen = 0; gen < a.n_gen; ++gen) {
-          const bool produce = gen + 1 < a.n_gen;
-          for (int isl = 0; isl < n_isl; ++isl) {
-            c.stream = (uint64_t)lc + (uint64_t)isl * a.n_lc;
-            double* const Pc = Pi + (size_t)isl * 2 * m + (size_t)cur * m;
-            double* const Pn = Pi + (size_t)isl * 2 * m + (size_t)(cur ^ 1) * m;
-            // fitness of every row (decode + forward model + chi^2)
-            if (threadIdx.x == 0) {
-                s_qcount = 0;
-                if (n_isl > 1) s_state = st_g[isl];
-            }
-            __syncthreads();
-            for (int base = 0; base < n_pop; base += per_pass) {
-                const int cand = base + group;
-                const bool valid = cand < n_pop;
-                const Cand k = group_candidate<true>(Pc, a.b, cand, valid, G);
-                double* A_row = (a.blend && valid) ? a.A_scr + ((size_t)blockIdx.x * n_pop + cand) * a.max_ep : nullptr;
-                double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, A_row, nullptr, queue,
-                                                        &s_qcount, a.qcap);
-                for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
-                if (g == 0 && valid) s_chi[cand] = chi;
-            }
-            __syncthreads();
-            if constexpr (MODE == SBLM_MIXED) {  // the block's queued epochs, in FP64
-                const unsigned n = min(s_qcount, a.qcap);
-                for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-                    const Deferred q = queue[i];
-                    const Cand k = candidate<true>(Pc, a.b, q.c);
-                    const float4 ep = view.s_ep[q.e];
-                    double* A_rq = a.blend ? a.A_scr + ((size_t)blockIdx.x * n_pop + q.c) * a.max_ep : nullptr;
-                    const double term = resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w,
-                                                     A_rq, nullptr, q.e, true);
-                    atomicAdd(&s_chi[q.c], term);
+            const bool produce = gen + 1 < a.n_gen;
+            for (int isl = 0; isl < n_isl; ++isl) {
+                c.stream = (uint64_t)lc + (uint64_t)isl * a.n_lc;
+                double* const Pc = Pi + (size_t)isl * 2 * m + (size_t)cur * m;
+                double* const Pn = Pi + (size_t)isl * 2 * m + (size_t)(cur ^ 1) * m;
+                // fitness of every row (decode + forward model + chi^2)
+                if (threadIdx.x == 0) {
+                    s_qcount = 0;
+                    if (n_isl > 1) s_state = st_g[isl];
                 }
                 __syncthreads();
-            }
-            if (a.blend) {  // Section 4.2: chi^2 of f A + (1 - f) with f profiled out, per candidate
                 for (int base = 0; base < n_pop; base += per_pass) {
                     const int cand = base + group;
-                    const double* Ar = a.A_scr + ((size_t)blockIdx.x * n_pop + min(cand, n_pop - 1)) * a.max_ep;
-                    double s_ab = 0.0, s_aa = 0.0;
-                    for (int e = g; cand < n_pop && e < n_ep; e += G) {
-                        double F, w;
-                        staged_fw<MODE>(view, e, F, w);
-                        const double ww = w * w, aa = Ar[e] - 1.0;
-                        s_ab += ww * aa * (F - 1.0);
-                        s_aa += ww * aa * aa;
-                    }
-                    for (int off = G / 2; off > 0; off >>= 1) {
-                        s_ab += __shfl_xor_sync(0xffffffffu, s_ab, off);
-                        s_aa += __shfl_xor_sync(0xffffffffu, s_aa, off);
-                    }
-                    const double f = blend_f(s_ab, s_aa, a.f_min);
-                    double chi = 0.0;
-                    for (int e = g; cand < n_pop && e < n_ep; e += G) {
-                        double F, w;
-                        staged_fw<MODE>(view, e, F, w);
-                        const double r = (F - 1.0) - f * (Ar[e] - 1.0);
-                        chi += w * w * r * r;
-                    }
+                    const bool valid = cand < n_pop;
+                    const Cand k = group_candidate<true>(Pc, a.b, cand, valid, G);
+                    double* A_row =
+                        (a.blend && valid) ? a.A_scr + ((size_t)blockIdx.x * n_pop + cand) * a.max_ep : nullptr;
+                    double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, A_row, nullptr, queue,
+                                                            &s_qcount, a.qcap);
                     for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
-                    if (g == 0 && cand < n_pop) {
-                        s_chi[cand] = chi;
-                        if (a.f_scr) a.f_scr[(size_t)blockIdx.x * n_pop + cand] = f;
-                    }
+                    if (g == 0 && valid) s_chi[cand] = chi;
                 }
                 __syncthreads();
-            }
-            if (a.mon_theta) {  // success monitor: every evaluated row against the reference
-                const double bound = a.mon_chi2[lc], f_ref = a.mon_f ? a.mon_f[lc] : -1.0;
-                for (int r = threadIdx.x; r < n_pop; r += blockDim.x) {
-                    if (!(s_chi[r] < bound)) continue;
-                    const double f = a.f_scr ? a.f_scr[(size_t)blockIdx.x * n_pop + r] : 1.0;
-                    if (monitor_match(Pc + (size_t)r * n_par, a.b, a.mon_theta + (size_t)lc * SBLM_NPAR, f,
-                                      f_ref, a.mon_tol))
-                        atomicCAS(&s_first, -1, gen);
-                }
-            }
-            // ranking, archive, stagnation
-            block_rank(s_chi, n_pop, a.n2, s_key, s_idx);
-            if (threadIdx.x == 0) {
-                double p_used = 0.0;
-                s_restart = block_bookkeeping(c, gen, s_key[0], Pc + (size_t)s_idx[0] * n_par, s_state, produce,
-                                              &p_used);
-                s_pmut = p_used;
-                if (n_isl > 1) {
-                    st_g[isl] = s_state;
-                    for (int j = 0; j < n_par; ++j) elite[isl * n_par + j] = Pc[(size_t)s_idx[0] * n_par + j];
-                }
-            }
-            __syncthreads();
-            if (produce) {
-                if (s_restart) {
-                    for (int e = threadIdx.x; e < m; e += blockDim.x)
-                        keys[e] = init_key(c, (uint64_t)(gen + 1), (uint64_t)e);
+                if constexpr (MODE == SBLM_MIXED) {  // the block's queued epochs, in FP64
+                    const unsigned n = min(s_qcount, a.qcap);
+                    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+                        const Deferred q = queue[i];
+                        const Cand k = candidate<true>(Pc, a.b, q.c);
+                        const float4 ep = view.s_ep[q.e];
+                        double* A_rq = a.blend ? a.A_scr + ((size_t)blockIdx.x * n_pop + q.c) * a.max_ep : nullptr;
+                        const double term = resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w,
+                                                         A_rq, nullptr, q.e, true);
+                        atomicAdd(&s_chi[q.c], term);
+                    }
                     __syncthreads();
-                    block_init_values(c, gen + 1, keys, m, Pn, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
-                                      a.n2);
-                } else {
-                    if (threadIdx.x == 0) {
-                        const double* e = Pc + (size_t)s_idx[0] * n_par;
-                        for (int j = 0; j < n_par; ++j) Pn[j] = e[j];
+                }
+                if (a.blend) {  // Section 4.2: chi^2 of f A + (1 - f) with f profiled out, per candidate
+                    for (int base = 0; base < n_pop; base += per_pass) {
+                        const int cand = base + group;
+                        const double* Ar = a.A_scr + ((size_t)blockIdx.x * n_pop + min(cand, n_pop - 1)) * a.max_ep;
+                        double s_ab = 0.0, s_aa = 0.0;
+                        for (int e = g; cand < n_pop && e < n_ep; e += G) {
+                            double F, w;
+                            staged_fw<MODE>(view, e, F, w);
+                            const double ww = w * w, aa = Ar[e] - 1.0;
+                            s_ab += ww * aa * (F - 1.0);
+                            s_aa += ww * aa * aa;
+                        }
+                        for (int off = G / 2; off > 0; off >>= 1) {
+                            s_ab += __shfl_xor_sync(0xffffffffu, s_ab, off);
+                            s_aa += __shfl_xor_sync(0xffffffffu, s_aa, off);
+                        }
+                        const double f = blend_f(s_ab, s_aa, a.f_min);
+                        double chi = 0.0;
+                        for (int e = g; cand < n_pop && e < n_ep; e += G) {
+                            double F, w;
+                            staged_fw<MODE>(view, e, F, w);
+                            const double r = (F - 1.0) - f * (Ar[e] - 1.0);
+                            chi += w * w * r * r;
+                        }
+                        for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
+                        if (g == 0 && cand < n_pop) {
+                            s_chi[cand] = chi;
+                            if (a.f_scr) a.f_scr[(size_t)blockIdx.x * n_pop + cand] = f;
+                        }
                     }
-                    for (int k = threadIdx.x; k < n_pop / 2; k += blockDim.x)
-                        offspring_pair(c, gen, Pc, s_idx, s_pmut, k, Pn);
+                    __syncthreads();
+                }
+                if (a.mon_theta) {  // success monitor: every evaluated row against the reference
+                    const double bound = a.mon_chi2[lc], f_ref = a.mon_f ? a.mon_f[lc] : -1.0;
+                    for (int r = threadIdx.x; r < n_pop; r += blockDim.x) {
+                        if (!(s_chi[r] < bound)) continue;
+                        const double f = a.f_scr ? a.f_scr[(size_t)blockIdx.x * n_pop + r] : 1.0;
+                        if (monitor_match(Pc + (size_t)r * n_par, a.b, a.mon_theta + (size_t)lc * SBLM_NPAR, f,
+                                          f_ref, a.mon_tol))
+                            atomicCAS(&s_first, -1, gen);
+                    }
+                }
+                // ranking, archive, stagnation
+                block_rank(s_chi, n_pop, a.n2, s_key, s_idx);
+                if (threadIdx.x == 0) {
+                    double p_used = 0.0;
+                    s_restart = block_bookkeeping(c, gen, s_key[0], Pc + (size_t)s_idx[0] * n_par, s_state, produce,
+                                                  &p_used);
+                    s_pmut = p_used;
+                    if (n_isl > 1) {
+                        st_g[isl] = s_state;
+                        for (int j = 0; j < n_par; ++j) elite[isl * n_par + j] = Pc[(size_t)s_idx[0] * n_par + j];
+                    }
                 }
                 __syncthreads();
+                if (produce) {
+                    if (s_restart) {
+                        for (int e = threadIdx.x; e < m; e += blockDim.x)
+                            keys[e] = init_key(c, (uint64_t)(gen + 1), (uint64_t)e);
+                        __syncthreads();
+                        block_init_values(c, gen + 1, keys, m, Pn, 0, blockDim.x, reinterpret_cast<uint64_t*>(s_key),
+                                          a.n2);
+                    } else {
+                        if (threadIdx.x == 0) {
+                            const double* e = Pc + (size_t)s_idx[0] * n_par;
+                            for (int j = 0; j < n_par; ++j) Pn[j] = e[j];
+                        }
+                        for (int k = threadIdx.x; k < n_pop / 2; k += blockDim.x)
+                            offspring_pair(c, gen, Pc, s_idx, s_pmut, k, Pn);
+                    }
+                    __syncthreads();
+                }
             }
-          }
             if (!produce) break;
             if (n_isl > 1 && a.mig_every > 0 && (gen + 1) % a.mig_every == 0) {
                 // Section 5.3, island EA: the elite of island i replaces the last row of the next
