@@ -93,8 +93,34 @@ def test_argument_validation_without_gpu(built):
     b = built.bounds([0, 5, 0, 0, 0.3, -4], [0, 100, 1, 6, 3, 0])  # lo == hi for t0
     p = built.params(n_pop=64, n_gen=10)
     assert lib.sblm_fit(None, None, None, 10, ctypes.byref(b), ctypes.byref(p), None, None, None, None) == 1
+    # the blended chi^2: negative sizes, an unknown precision, missing buffers
+    assert lib.sblm_chi2_blend(None, -1, None, None, None, 5, None, None, 0, None) == 1
+    assert lib.sblm_chi2_blend(None, 2, None, None, None, 5, None, None, 7, None) == 1
+    assert lib.sblm_chi2_blend(None, 2, None, None, None, 5, None, None, 0, None) == 1
+    assert b"NULL" in lib.sblm_last_error()
+    # the single-lightcurve fitter takes neither the blend flag nor islands (batched fitters only)
+    b = built.bounds([-20, 5, 0, 0, 0.3, -4], [20, 100, 1, 6, 3, 0])
+    p = built.params(n_pop=64, n_gen=10, precision="mixed+blend")
+    assert lib.sblm_fit(None, None, None, 10, ctypes.byref(b), ctypes.byref(p), None, None, None, None) == 1
+    assert b"SBLM_BLEND" in lib.sblm_last_error()
+    p = built.params(n_pop=64, n_gen=10, n_islands=2)
+    assert lib.sblm_fit(None, None, None, 10, ctypes.byref(b), ctypes.byref(p), None, None, None, None) == 1
+    assert b"islands" in lib.sblm_last_error()
     # zero-size work is a successful no-op
     assert lib.sblm_magnification(None, 0, None, 0, None, None, 0, None) == 0
+    assert lib.sblm_chi2_blend(None, 0, None, None, None, 5, None, None, 0, None) == 0
+
+
+def test_precision_strings():
+    from paper_1208_4830_gb300 import sblm
+
+    assert sblm._precision("fp64") == 0 and sblm._precision("mixed") == 1 and sblm._precision("fp32") == 2
+    assert sblm._precision("mixed+blend") == 1 | sblm.BLEND and sblm._precision("fp64+blend") == sblm.BLEND
+    assert sblm._precision(17) == 17
+    with pytest.raises(ValueError):
+        sblm._precision("mixed+islands")
+    p = sblm.params()
+    assert (p.n_islands, p.migration_interval) == (1, 20)
 
 
 def test_binding_refuses_to_run_without_library(tmp_path):
