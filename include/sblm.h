@@ -50,8 +50,9 @@ typedef enum {
 enum {
     SBLM_FP64 = 0,  /* everything in FP64 */
     SBLM_MIXED = 1, /* FP32 quintic solve; FP64 re-solve and polish of an epoch when triggered
-                       (|det J| < 1e-3 at an image, two roots closer than 1e-4, or an ambiguous
-                       image classification); chi^2 accumulated in FP64 */
+                       (|det J| < 3e-2 at an image or at a rejected root that nearly solves
+                       the lens equation, two roots closer than 1e-4, or an ambiguous image
+                       classification); chi^2 accumulated in FP64 */
     SBLM_FP32 = 2   /* FP32 solve, no FP64 re-solve; chi^2 accumulated in FP64 */
 };
 
@@ -135,7 +136,8 @@ void sblm_ea_params_default(sblm_ea_params* p);
  *                           3 (or 5) smallest residuals, bit 1 = an FP64 re-solve ran (MIXED),
  *                           bit 2 = the root iteration hit its cap, bit 3 = a rejected root was
  *                           nearly an image (FP32: a close image pair may be unresolved), bit 4 =
- *                           an image has |det J| < 1e-3, bit 5 = two images closer than 1e-4
+ *                           an image (or a rejected root with a relative lens-equation residual
+ *                           below 0.05) has |det J| < 3e-2, bit 5 = two images closer than 1e-4
  *                           (bits 4-5: FP32 and MIXED; in MIXED any of bits 0 and 2-5 of the FP32
  *                           solution triggers the FP64 re-solve, and they stay set beside bit 1)
  * n_cand >= 0, n_ep >= 0 (zero sizes return SBLM_OK without a launch). Host theta rows are checked

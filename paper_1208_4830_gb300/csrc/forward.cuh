@@ -192,6 +192,9 @@ struct EpochOut {
     T A;         // sum of 1/|det J| over the images
     T min_det;   // smallest |det J| over the images
     T min_gap;   // smallest distance between two images
+    T min_det_rej;  // smallest |det J| over the rejected roots that nearly solve the lens equation
+                    // (relative residual below kSpurious): a pair of images that the arithmetic
+                    // failed to converge sits next to the critical curve
     int sweeps;  // root-iteration sweeps spent (diagnostics)
     uint8_t flag;
 };
@@ -372,17 +375,27 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
         rej = fmin(rej, r2[i] > lens2 ? r2[i] : T(INFINITY));
     }
     if (rej < T(Tol<T>::ambiguous) * T(Tol<T>::ambiguous)) out.flag |= FLAG_AMBIGUOUS;
+    T mdr = T(INFINITY);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if (!acc[i] && r2[i] <= T(kSpurious) * T(kSpurious)) mdr = fmin(mdr, fabs(det[i]));
+    out.min_det_rej = mdr;
     out.A = A;
     out.min_det = md;
     out.min_gap = sqrt_(min_gap2);
     return out;
 }
 
-// When two or more roots lie closer to the secondary than kLocalFrac * d, they are refined on the
-// quintic written in the secondary's frame (masses (q, 1) at (0, -d), source zeta - d), whose
-// low-order coefficients carry q with full relative precision: in the primary's frame a cluster
-// of roots next to the secondary (a few q apart for a small q) is not resolved in FP32.
+// When two or more roots lie closer to the secondary than max(kLocalFrac d, min(sqrt q,
+// kLocalCap d)), they are refined on the quintic written in the secondary's frame (masses (q, 1)
+// at (0, -d), source zeta - d), whose low-order coefficients carry q with full relative
+// precision: in the primary's frame a cluster of roots next to the secondary (a few q apart for a
+// small q) is not resolved in FP32. The images of a source at the secondary's (planetary)
+// caustic spread over about the secondary's Einstein radius sqrt(q), which exceeds kLocalFrac d
+// when d is small; left in the primary's frame such a cluster stops at the noise level of the
+// Horner evaluation with two roots far from the images.
 constexpr float kLocalFrac = 0.1f;
+constexpr float kLocalCap = 0.3f;
 
 // One epoch in arithmetic T: quintic, roots (warm from the previous epoch's roots when `warm`),
 // images, magnification. Updates z (the polynomial roots) and `warm`. The root iteration has a
@@ -444,7 +457,8 @@ __device__ __forceinline__ EpochOut<T> solve_epoch(cx<T> zeta, T d, T q, cx<T> z
             continue;
         }
         if (!kTwoFrames) break;
-        const T lim2 = T(kLocalFrac) * T(kLocalFrac) * d * d;
+        const T rl = fmax(T(kLocalFrac) * d, fmin(sqrt_(q), T(kLocalCap) * d));
+        const T lim2 = rl * rl;
         local = 0;
 #pragma unroll
         for (int i = 0; i < 5; ++i) local |= (norm2(z[i] - dd) < lim2 ? 1u : 0u) << i;

@@ -17,9 +17,11 @@ struct Bounds {
     double hi[SBLM_NPAR];
 };
 
-// MIXED: an epoch is re-solved in FP64 when an image has |det J| below this, when two images
-// are closer than the gap trigger, or when the FP32 image selection was ambiguous
-constexpr float kMixedDetTrigger = 1e-3f;
+// MIXED: an epoch is re-solved in FP64 when an image, or a rejected root that nearly solves the
+// lens equation, has |det J| below this (next to a caustic FP32 loses accuracy, and an image pair
+// it failed to converge sits next to the critical curve), when two images are closer than the
+// gap trigger, or when the FP32 image selection was ambiguous
+constexpr float kMixedDetTrigger = 3e-2f;
 constexpr float kMixedGapTrigger = 1e-4f;
 
 // largest lightcurve staged in shared memory per block (larger ones are read from global memory)

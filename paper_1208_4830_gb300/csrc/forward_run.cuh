@@ -176,7 +176,7 @@ __device__ __forceinline__ double eval_run(const Cand& k, bool valid, int c_tag,
                 const float tau = diff_ff(ep.x, ep.y, t0h, t0l) * itE;
                 const cx<float> zeta = mk<float>(tau * sa + u0 * ca, -tau * ca + u0 * sa);
                 EpochOut<float> o = solve_epoch<float>(zeta, d, q, z, warm);
-                o.flag |= (o.min_det < kMixedDetTrigger ? FLAG_NEAR_DET : 0) |
+                o.flag |= (fminf(o.min_det, o.min_det_rej) < kMixedDetTrigger ? FLAG_NEAR_DET : 0) |
                           (o.min_gap < kMixedGapTrigger ? FLAG_NEAR_GAP : 0);
                 if (MODE == SBLM_MIXED) defer = o.flag != 0;
                 why = o.flag;
