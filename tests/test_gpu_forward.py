@@ -183,11 +183,11 @@ def test_invalid_host_data_rejected(lib):
 
 def test_mixed_chi2_of_the_full_sweep_against_fp64(lib):
     """The whole 4096 x 2000 sweep (10% of the trajectories aimed at caustics), every row, MIXED
-    chi^2 against the device's FP64 chi^2 (itself held to the oracle above). Known gap: on a few
-    caustic-crossing rows FP32 finds three images where a fold has just made five, with the two
-    missed roots far enough from the lens equation that no re-solve trigger fires, so those
-    epochs lose the bright pair (on this sweep 0.6% of the rows are off by more than 1e-3 and
-    0.2% by more than 1e-2). The bound below holds that share."""
+    chi^2 against the device's FP64 chi^2 (itself held to the oracle above). This caught epochs
+    where FP32 found three images of five with nothing to trigger a re-solve (a planetary-caustic
+    cluster left in the primary's frame, an unconverged pair next to the critical curve): before
+    the |det J| trigger on near-image rejected roots and the sqrt(q) frame radius 0.2% of the rows
+    were off by more than 1e-2, the worst by 96%; now no row is (worst 3.3e-3 when written)."""
     sw = synth.forward_sweep(n_cand=4096, n_ep=2000, seed=0)
     th, t = dev(sw.theta), dev(sw.t)
     A_true = osb.magnification(sw.truth[None, :], sw.t)[0]
@@ -197,7 +197,7 @@ def test_mixed_chi2_of_the_full_sweep_against_fp64(lib):
     cm = lib.chi2(th, t, dev(flux), dev(sigma), "mixed").cpu().numpy()
     err = np.abs(cm - c64) / c64
     assert np.median(err) < 1e-6
-    assert np.mean(err > 1e-3) <= 0.01, np.mean(err > 1e-3)
-    assert np.mean(err > 1e-2) <= 0.005, np.mean(err > 1e-2)
+    assert err.max() <= 1e-2, (int(np.argmax(err)), err.max())
+    assert np.mean(err > 1e-3) <= 0.005, np.mean(err > 1e-3)
     # the trajectories not aimed at a caustic (most of the sweep) rarely meet one
-    assert np.mean(err[~sw.forced] > 1e-3) <= 0.005
+    assert np.mean(err[~sw.forced] > 1e-3) <= 0.002
