@@ -78,3 +78,16 @@ def test_re_solve_share_stays_small(loop):
     rows = np.nonzero(~sw.forced)[0][:120]
     _, fl, _ = host_build.run(exe, sw.theta[rows], sw.t, 8, wd)
     assert np.mean(fl != 0) < 0.01, np.mean(fl != 0)
+
+
+def test_fp64_loop_meets_the_device_parity_bound(loop):
+    """The FP64 epoch loop of the host build against the oracle on the 37 x 1037 sweep: relative
+    1e-10 wherever the oracle's smallest |det J| is at least 1e-3, as the device test asks."""
+    wd, exe = loop
+    sw = synth.forward_sweep(n_cand=37, n_ep=1037, seed=3, caustic_frac=0.3)
+    A_ref, info = osb.magnification(sw.theta, sw.t, return_info=True)
+    _, _, A64 = host_build.run(exe, sw.theta, sw.t, 5, wd)
+    ok = ~info["flag"] & (info["min_det"] >= 1e-3)
+    assert ok.mean() >= 0.9
+    err = np.abs(A64 - A_ref) / A_ref
+    assert err[ok].max() <= 1e-10, err[ok].max()
