@@ -506,11 +506,19 @@ def fit_batch_monitored(t, flux, sigma, offsets, lo, hi, p, theta_ref, chi2_max,
     best = np.empty((n_lc, 6))
     best_chi2 = np.empty(n_lc)
     first = np.empty(n_lc, dtype=np.int32)
-    ref = np.ascontiguousarray(theta_ref, dtype=np.float64)
-    cmax = np.ascontiguousarray(chi2_max, dtype=np.float64)
-    fr = None if f_ref is None else np.ascontiguousarray(f_ref, dtype=np.float64)
-    mon = BatchMonitor(ref.ctypes.data, None if fr is None else fr.ctypes.data, cmax.ctypes.data, float(rel_tol),
-                       first.ctypes.data)
+
+    def f64(x):  # float64 torch tensors (host or device) pass through; anything else becomes a float64 array
+        if hasattr(x, "data_ptr"):
+            import torch
+
+            if x.dtype != torch.float64:
+                raise TypeError("monitor arrays must be float64")
+            return x.contiguous()
+        return np.ascontiguousarray(x, dtype=np.float64)
+
+    ref, cmax = _ptr(f64(theta_ref)), _ptr(f64(chi2_max))
+    fr = _ptr(None if f_ref is None else f64(f_ref))
+    mon = BatchMonitor(ref[0], fr[0], cmax[0], float(rel_tol), first.ctypes.data)
     tuning = _tuning(tuning, t, flux, sigma, offsets, lo, hi, p, stream)
     a = [_ptr(x) for x in (t, flux, sigma, offsets, weights)]
     s = _stream(stream, t, flux, sigma, weights)
