@@ -524,33 +524,44 @@ def run_e2e(sblm, sw, P0, flux, sigma, args):
             "path": "sblm_chi2_genes + sblm_ea_generation on pinned host buffers"}
 
 
-def cpu_baseline(sw, flux, sigma, seconds):
-    """The FP64 oracle on the host: chi^2 of as many sweep candidates as fit in about
-    `seconds`, one process, one thread."""
+def oracle_operator_seconds():
+    """Seconds the oracle takes for the operators of one generation on the full population."""
     from oracle import ea as oea
+
+    P0 = build_inputs()[1]
+    chi = np.random.default_rng(0).uniform(0, 1e4, N_CAND)
+    op = oea.EAParams(n_pop=N_CAND, seed=0)
+    t0 = time.perf_counter()
+    oea.generation(P0, chi, oea.new_state(op), op, 0)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(sw, flux, sigma, seconds, chunk=16, t_ops=None):
+    """The FP64 oracle on the host: chi^2 of as many sweep candidates as fit in about
+    `seconds` (in chunks of `chunk`), one process, one thread, plus the operators of one
+    generation on the full population (timed here unless `t_ops` is given), amortised per
+    magnification."""
     from oracle import sblm as osb
 
     n_done, t_spent = 0, 0.0
     rows = np.arange(N_CAND)
     k = 0
     while t_spent < seconds and k < N_CAND:
-        sel = rows[k : k + 16]
+        sel = rows[k : k + chunk]
         t0 = time.perf_counter()
         osb.chi2(sw.theta[sel], sw.t, flux, sigma)
         t_spent += time.perf_counter() - t0
         n_done += sel.size
-        k += 16
-    # the operators of one generation on the full population, amortised per magnification
-    P0 = build_inputs()[1]
-    chi = np.random.default_rng(0).uniform(0, 1e4, N_CAND)
-    op = oea.EAParams(n_pop=N_CAND, seed=0)
-    t0 = time.perf_counter()
-    oea.generation(P0, chi, oea.new_state(op), op, 0)
-    t_ops = time.perf_counter() - t0
+        k += chunk
+    if t_ops is None:
+        t_ops = oracle_operator_seconds()
     per_mag = t_spent / (n_done * N_EP) + t_ops / (N_CAND * N_EP)
     return {"value": 1.0 / per_mag, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_done} of {N_CAND} candidates x {N_EP} epochs (numpy FP64, companion-matrix roots) "
                       f"+ one generation of operators on all {N_CAND} rows, {t_spent + t_ops:.1f} s"}
+
+
+REFERENCE_SECONDS = 120.0
 
 
 def run_reference(args):
@@ -564,10 +575,13 @@ def run_reference(args):
     A_true = osb.magnification(sw.truth[None, :], sw.t)[0]
     sigma = sw.sigma_frac * A_true
     flux = A_true + sigma * sw.z
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    # the whole run takes about REFERENCE_SECONDS whatever --steps and --warmup are: each step
+    # times as many single candidates as fit in its share; the operators are timed once
+    per_step = max(0.02, REFERENCE_SECONDS / max(1, args.steps + args.warmup))
+    t_ops = oracle_operator_seconds()
     vals = []
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(sw, flux, sigma, per_step)
+        cb = cpu_baseline(sw, flux, sigma, per_step, chunk=1, t_ops=t_ops)
         if k >= args.warmup:
             vals.append(cb["value"])
     value = float(np.mean(vals))
