@@ -352,7 +352,7 @@ def run_fits(sblm, args):
     out = {"workload": f"held-out synthetic curves (sweep priors, 10% through caustics), {FIT_EP} epochs, "
                        f"2% noise; N_pop {FIT_POP} x {FIT_GEN} generations + amoeba polish ({FIT_POLISH} "
                        f"chi^2 evaluations); batched persistent fitter",
-           "success_criterion": "dchi2_per_dof_lt_1 (paper, Section 4.1); dchi2_le_1 and strict also reported",
+           "success_criterion": "dchi2_per_dof_lt_1 (paper, Section 4.2); dchi2_le_1 and strict also reported",
            "proposal": proposal}
     out["seeded_mixed"] = arm("mixed", SEED_FRAC, FIT_LCS)
     out["plain_mixed"] = arm("mixed", 0.0, FIT_LCS)
@@ -372,8 +372,8 @@ def run_fits(sblm, args):
 # t0 +- (2..3) tE, sigma 0.01 mag; success per number of peaks, EA + amoeba as in Table 2
 PAPER_LCS, PAPER_POP, PAPER_GEN = 256, 1000, 3000
 PAPER_TABLE2_EA_AMOEBA = {"1": [97, 100], "2": [98, 100], "3": [97, 98], "4": [94, 94]}  # strict, weak (%)
-# the paper's noisy, blended test (Section 4.3): as above with epochs drawn at random, the noise
-# model of Section 2.2 (m0 in Table 1's [18, 22]) and a blending fraction f in (0, 1], fitted
+# the paper's noisy, blended test (Section 4.4): as above with epochs drawn at random, the noise
+# model of Section 2.4 (m0 in Table 1's [18, 22]) and a blending fraction f in (0, 1], fitted
 # with the blended chi^2 (f profiled out); Table 3 reports EA + amoeba only
 PAPER_TABLE3_EA_AMOEBA = {"1": [95, 98], "2": [96, 99], "3": [90, 97], "4": [87, 99]}  # strict, weak (%)
 
@@ -474,7 +474,7 @@ def run_noisy_blended_workload(sblm, w):
                                          flux[b.offsets[i] : b.offsets[i + 1]], sigma[b.offsets[i] : b.offsets[i + 1]],
                                          "fp64")[0][0] for i in range(PAPER_LCS)])
     out = {"workload": f"{PAPER_LCS} noisy, blended curves of the paper's second test (Table 1 ranges, 100 random "
-                       f"epochs, noise model of Section 2.2, f in (0, 1]); blended chi^2 with f profiled out; "
+                       f"epochs, noise model of Section 2.4, f in (0, 1]); blended chi^2 with f profiled out; "
                        f"N_pop {PAPER_POP} x {PAPER_GEN} generations + amoeba ({FIT_POLISH} evaluations)",
            "curves_per_peak_class": {str(k): int(np.sum(peaks == k)) for k in (1, 2, 3, 4)},
            "paper_table3_ea_amoeba_strict_weak_pct": PAPER_TABLE3_EA_AMOEBA}

@@ -58,7 +58,7 @@ enum {
 
 /* OR-ed into sblm_ea_params.precision of the batched fitters (sblm_fit_batch*), or into the
  * precision argument of sblm_polish_batch: each candidate's chi^2 is that of the blended model
- * f A + (1 - f) (Section 4.2, Eq. blend; flux normalised to the baseline) with f profiled out as
+ * f A + (1 - f) (Section 4.4, Eq. blend; flux normalised to the baseline) with f profiled out as
  * in sblm_chi2_blend, so best_chi2 / chi2_out hold that chi^2 and the six returned parameters
  * are those of the lens; sblm_chi2_blend on them gives f. Needs 8 bytes of device scratch per
  * epoch per population row per SM. The single-lightcurve calls (sblm_fit, sblm_ea_*) reject it
@@ -297,7 +297,7 @@ typedef struct {
 } sblm_batch_monitor;
 
 /*
- * chi^2 of the blended model of Section 4.2 (Eq. blend), A_obs = f A + (1 - f), for each
+ * chi^2 of the blended model of Section 4.4 (Eq. blend), A_obs = f A + (1 - f), for each
  * parameter row, with the blending fraction profiled out: the paper notes its least-squares value
  * follows from a linear equation. With a_k = A_k - 1, b_k = F_k - 1 and w_k = 1/sigma_k^2,
  * f = sum w a b / sum w a^2 clamped to [SBLM_BLEND_F_MIN, 1] (f = 1 when sum w a^2 = 0), and

@@ -271,20 +271,82 @@ def generation(P, chi2, state, params, gen):
     return P_next
 
 
-def run(fitness, n_par, params, trace=None):
-    """Reference driver: N_gen evaluations of ``fitness(P) -> chi^2``; returns the archive."""
+def run(fitness, n_par, params, trace=None, solutions=None):
+    """Reference driver: N_gen evaluations of ``fitness(P) -> chi^2``; returns the archive.
+    ``solutions`` (a SolutionArchive) is offered each generation's ranked population."""
     state = new_state(params)
     P = init_population(params.n_pop, n_par, params, 0)
     for g in range(params.n_gen):
         chi2 = np.asarray(fitness(P), dtype=np.float64)
         if trace is not None:
             trace.append((g, float(np.nanmin(chi2)), state.p_mut, state.n_restarts))
+        if solutions is not None:
+            Pr, cr, _ = rank(P, chi2)
+            solutions.offer_ranked(Pr, cr)
         if g == params.n_gen - 1:
             Pr, cr, _ = rank(P, chi2)
             archive(state, Pr, cr)
         else:
             P = generation(P, chi2, state, params, g)
     return state
+
+
+# ---------------------------------------------------------------------------------------------
+# Several solutions (Section 3.1: the explored phenotypes that meet a fitness criterion, rather
+# than only the fittest; Appendix A, "Outputs")
+# ---------------------------------------------------------------------------------------------
+class SolutionArchive:
+    """The ``size`` fittest mutually distinct solutions seen during a run. The paper leaves the
+    rule open; the reading here: two solutions are the same when every gene differs by at most
+    ``radius``; an offered row that matches an archived solution replaces it when fitter (and is
+    dropped otherwise); a new solution enters while there is room, or in place of the least fit
+    one when it is fitter. After a replacement the archive is merged again, so that it stays
+    free of matching pairs. Entries are kept sorted by chi^2 (stable)."""
+
+    def __init__(self, size, radius):
+        self.size, self.radius = int(size), float(radius)
+        self.genes, self.chi2 = [], []
+
+    def _same(self, a, b):
+        return bool(np.all(np.abs(np.asarray(a) - np.asarray(b)) <= self.radius))
+
+    def offer(self, genes, chi2):
+        chi2 = float(chi2)
+        if not math.isfinite(chi2):
+            return
+        genes = np.array(genes, dtype=np.float64)
+        for k, g in enumerate(self.genes):
+            if self._same(g, genes):
+                if chi2 < self.chi2[k]:
+                    self.genes[k], self.chi2[k] = genes, chi2
+                    self._merge(k)
+                    self._sort()
+                return
+        if len(self.genes) < self.size:
+            self.genes.append(genes)
+            self.chi2.append(chi2)
+        elif chi2 < self.chi2[-1]:
+            self.genes[-1], self.chi2[-1] = genes, chi2
+        else:
+            return
+        self._sort()
+
+    def _merge(self, k):
+        """Drop the entries that now match entry k (it is the fitter of each such pair)."""
+        keep = [i for i in range(len(self.genes)) if i == k or not self._same(self.genes[i], self.genes[k])]
+        self.genes = [self.genes[i] for i in keep]
+        self.chi2 = [self.chi2[i] for i in keep]
+
+    def _sort(self):
+        order = sorted(range(len(self.chi2)), key=lambda i: self.chi2[i])
+        self.genes = [self.genes[i] for i in order]
+        self.chi2 = [self.chi2[i] for i in order]
+
+    def offer_ranked(self, P_ranked, chi2_ranked, top=None):
+        """Offer the ``top`` fittest rows of a ranked population (all rows by default), fittest first."""
+        n = len(chi2_ranked) if top is None else min(top, len(chi2_ranked))
+        for i in range(n):
+            self.offer(P_ranked[i], chi2_ranked[i])
 
 
 # ---------------------------------------------------------------------------------------------

@@ -100,7 +100,7 @@ def nelder_mead(fun, x0, f0=None, maxfev=1000, delta=DELTA):
 
 def polish_sblm(t, flux, sigma, lo, hi, genes, maxfev, chi2_start=None, blend=False):
     """Amoeba fine-tuning of one SBLM solution given by its genes: (genes, chi^2, evaluations).
-    With ``blend`` the objective is the chi^2 of the blended model of Section 4.2 with the
+    With ``blend`` the objective is the chi^2 of the blended model of Section 4.4 with the
     blending fraction profiled out (``sblm.chi2_blend``)."""
     from . import ea, sblm
 

@@ -24,7 +24,7 @@ What it computes, in the paper's order (Rajpaul 2012, Section 2.2):
    the Jacobian of the lens map and for the single-lens (Paczynski) limit;
 7. total magnification A = sum_i A_i (flux of a unit, unblended source), and the chi^2 of
    Section 4.1, sum_k ((F_k - A_k) / sigma_k)^2;
-8. the blended model of Section 4.2, f A + (1 - f), with f profiled out in closed form
+8. the blended model of Section 4.4, f A + (1 - f), with f profiled out in closed form
    (``blend_fit``; flux normalised to the baseline).
 
 Readings where the paper is silent:
@@ -293,7 +293,7 @@ BLEND_F_MIN = 1e-3  # smallest blending fraction of the profiled fit
 
 
 def blend_fit(A, flux, sigma, f_min=BLEND_F_MIN):
-    """Blended model of Section 4.2 (Eq. blend), A_obs = f A + (1 - f), with the fraction f
+    """Blended model of Section 4.4 (Eq. blend), A_obs = f A + (1 - f), with the fraction f
     profiled out: the paper notes that its least-squares value follows from a linear equation.
     With a = A - 1, b = F - 1 and w = 1/sigma^2, chi^2(f) = sum w (b - f a)^2 is least at
     f = sum w a b / sum w a^2, clamped to [f_min, 1]. Sums run over the last axis in order.

@@ -62,7 +62,7 @@ struct BatchArgs {
     uint64_t prop_seed;
     int polish_fev;      // amoeba fine-tuning of the archive's best (0: none), a separate launch
     double* best_genes;  // [n_lc][6] genes of best_chi2
-    int blend;           // chi^2 of the blended model with f profiled out (Section 4.2)
+    int blend;           // chi^2 of the blended model with f profiled out (Section 4.4)
     double f_min;
     double* A_scr;       // blend: per block n_pop x max_ep magnifications
     int n_isl;           // island EA (Section 5.3): populations per lightcurve (1: the paper's panmictic EA)
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                     }
                     __syncthreads();
                 }
-                if (a.blend) {  // Section 4.2: chi^2 of f A + (1 - f) with f profiled out, per candidate
+                if (a.blend) {  // Section 4.4: chi^2 of f A + (1 - f) with f profiled out, per candidate
                     for (int base = 0; base < n_pop; base += per_pass) {
                         const int cand = base + group;
                         const double* Ar = a.A_scr + ((size_t)blockIdx.x * n_pop + min(cand, n_pop - 1)) * a.max_ep;

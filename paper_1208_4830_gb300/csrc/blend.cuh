@@ -1,4 +1,4 @@
-// blend.cuh -- the blended model of Section 4.2 (Eq. blend), A_obs = f A + (1 - f), with the
+// blend.cuh -- the blended model of Section 4.4 (Eq. blend), A_obs = f A + (1 - f), with the
 // blending fraction profiled out: with a = A - 1, b = F - 1 and w = 1/sigma^2 the least-squares f
 // is sum w a b / sum w a^2 (clamped to [f_min, 1]; 1 when sum w a^2 = 0) and the chi^2 is
 // sum w (b - f a)^2. Callers sum the epochs in a fixed order (per thread, then a fixed tree).

@@ -75,7 +75,7 @@ __device__ double block_chi2(const double* g, const Bounds& b, const LCView& vie
             chi += resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w, A_row, nullptr, q.e, true);
         }
     }
-    if (A_row) {  // Section 4.2: f A + (1 - f) with f profiled out
+    if (A_row) {  // Section 4.4: f A + (1 - f) with f profiled out
         __syncthreads();
         double s_ab = 0.0, s_aa = 0.0;
         for (int e = threadIdx.x; e < n_ep; e += blockDim.x) {

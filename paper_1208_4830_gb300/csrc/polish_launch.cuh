@@ -32,7 +32,7 @@ struct PolishArgs {
     int maxfev;
     Deferred* queue;     // MIXED: qcap entries per block
     unsigned qcap;
-    int blend;           // chi^2 of the blended model with f profiled out (Section 4.2)
+    int blend;           // chi^2 of the blended model with f profiled out (Section 4.4)
     double f_min;
     double* A_scr;       // blend: per block A_stride magnifications
     int A_stride;

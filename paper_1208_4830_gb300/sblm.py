@@ -27,7 +27,7 @@ NPAR = 6
 MAX_NPAR = 16
 MAX_WINDOW = 15
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
-BLEND = 16  # OR-ed into a precision: chi^2 of the blended model with f profiled out (Section 4.2)
+BLEND = 16  # OR-ed into a precision: chi^2 of the blended model with f profiled out (Section 4.4)
 BLEND_F_MIN = 1e-3
 STATUS = {0: "SBLM_OK", 1: "SBLM_EINVAL", 2: "SBLM_ENOMEM", 3: "SBLM_ECUDA", 4: "SBLM_ETIMEOUT", 5: "SBLM_ENUMERIC"}
 
@@ -278,7 +278,7 @@ def chi2(theta, t, flux, sigma, precision="fp64", out=None, stream=None):
 
 def chi2_blend(theta, t, flux, sigma, precision="fp64", out=None, f_out=None, stream=None):
     """(chi^2, f) of each parameter row against the lightcurve for the blended model
-    f A + (1 - f) of Section 4.2 with the blending fraction f profiled out."""
+    f A + (1 - f) of Section 4.4 with the blending fraction f profiled out."""
     n_cand, n_ep = int(theta.shape[0]), int(t.shape[0])
     if out is None:
         out = _like(theta, (n_cand,), np.float64)

@@ -260,7 +260,7 @@ def count_peaks(A, rel_prominence=0.01):
     return n
 
 
-# Section 2.2's photometric noise model: log10 sigma_I = slope * m_I + intercept (magnitudes)
+# Section 2.4's photometric noise model: log10 sigma_I = slope * m_I + intercept (magnitudes)
 NOISE_SLOPE, NOISE_INTERCEPT = 0.3416, -7.7095
 M0_RANGE = (18.0, 22.0)  # Table 1: unlensed magnitude
 
@@ -291,7 +291,7 @@ class NoisyBlendedBatch:
 
 
 def noisy_blended_batch(n_lc=512, seed=0, n_ep=100):
-    """Curves shaped like the paper's noisy, blended test (Section 4.3): parameters as in
+    """Curves shaped like the paper's noisy, blended test (Section 4.4): parameters as in
     paper_batch (Table 1 ranges, q uniform in [0.1, 1]), m0 uniform over Table 1's [18, 22], a
     blending fraction f uniform on (0, 1], and n_ep epochs drawn uniformly on (t_start, t_end)
     (sorted), with (t_start - t0)/tE in (-3, -2) and (t_end - t0)/tE in (2, 3)."""

@@ -1,4 +1,4 @@
-"""The blended model of Section 4.2 (Eq. blend) on the device: sblm_chi2_blend, and the
+"""The blended model of Section 4.4 (Eq. blend) on the device: sblm_chi2_blend, and the
 SBLM_BLEND flag of the batched fitter and of the amoeba, against the oracle (oracle/sblm.py
 blend_fit and chi2_blend, oracle/polish.py with blend=True).
 
@@ -151,7 +151,7 @@ def test_fp64_blend_polish_follows_the_oracle_simplex(lib):
 
 
 def test_blend_fit_recovers_noisy_blended_events(lib):
-    """Section 4.3's noisy, blended curves (random epochs, the noise model of Section 2.2, f in
+    """Section 4.4's noisy, blended curves (random epochs, the noise model of Section 2.4, f in
     (0, 1]), EA + amoeba on the blended chi^2: most fits meet the paper's criterion
     (delta chi^2 / nu < 1, nu = 100 - 7), and fitting without the blend term does worse."""
     n = 24

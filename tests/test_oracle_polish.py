@@ -66,7 +66,7 @@ def test_first_step_by_hand():
 
 
 def test_blended_objective_recovers_a_blended_curve():
-    """Section 4.2's blended model: from near the truth of a noise-free curve diluted to f = 0.35,
+    """Section 4.4's blended model: from near the truth of a noise-free curve diluted to f = 0.35,
     the amoeba on the profiled-f objective returns to the truth (chi^2 ~ 0, f recovered), while
     the unblended objective is left with a large chi^2."""
     from oracle import ea

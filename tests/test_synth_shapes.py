@@ -37,7 +37,7 @@ def test_heldout_truths_inside_the_fit_domain():
 
 
 def test_noisy_blended_batch_follows_the_paper_setup():
-    """Section 4.3's changes to the test: random epochs, the noise model of Section 2.2, blending."""
+    """Section 4.4's changes to the test: random epochs, the noise model of Section 2.4, blending."""
     b = synth.noisy_blended_batch(50, seed=6)
     assert b.offsets[-1] == 50 * 100
     assert np.all((b.f > 0) & (b.f <= 1)) and np.all((b.m0 >= 18) & (b.m0 <= 22))
