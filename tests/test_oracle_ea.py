@@ -231,3 +231,40 @@ def test_migrants_reach_the_neighbour():
             elite = pops[g][i][int(np.argmin(chi))]
             assert np.array_equal(pops[g + 1][(i + 1) % 3][-1], elite)
             assert states[(i + 1) % 3].best_chi2 <= chi.min()
+
+
+def test_solution_archive_by_hand():
+    arc = ea.SolutionArchive(size=3, radius=0.1)
+    steps = [([0.5, 0.5], 10.0), ([0.55, 0.5], 8.0), ([0.9, 0.9], 12.0), ([0.1, 0.1], 5.0), ([0.3, 0.3], 20.0),
+             ([0.3, 0.3], 9.0), ([0.62, 0.45], 7.0), ([0.65, 0.5], 6.5), ([0.64, 0.48], 6.6), ([0.2, 0.9], np.nan)]
+    for g, c in steps:
+        arc.offer(g, c)
+    # 0.55 replaced 0.5 (same solution, fitter); 12 was pushed out by 9; 0.62 then 0.65 replaced
+    # the 0.55 entry; 6.6 matched but was not fitter; NaN is never archived
+    assert arc.chi2 == [5.0, 6.5, 9.0]
+    np.testing.assert_array_equal(np.array(arc.genes), [[0.1, 0.1], [0.65, 0.5], [0.3, 0.3]])
+    # a fitter solution matching two entries takes the first and absorbs the other
+    arc = ea.SolutionArchive(size=4, radius=0.1)
+    arc.offer([0.1, 0.1], 5.0)
+    arc.offer([0.3, 0.3], 9.0)
+    arc.offer([0.2, 0.2], 4.0)
+    assert arc.chi2 == [4.0] and np.array_equal(arc.genes[0], [0.2, 0.2])
+
+
+def test_solution_archive_over_a_run():
+    """Over a whole run on a function with three wells: the archive's first entry is the run's
+    best, entries are sorted and pairwise distinct."""
+    wells = np.array([[0.2, 0.2, 0.5], [0.8, 0.3, 0.5], [0.5, 0.85, 0.2]])
+    depth = np.array([0.0, 0.001, 0.002])
+
+    def f(P):
+        d2 = ((P[:, None, :] - wells[None]) ** 2).sum(-1) + depth[None]
+        return d2.min(1)
+
+    arc = ea.SolutionArchive(size=8, radius=0.05)
+    st = ea.run(f, 3, params(n_pop=40, n_gen=120, seed=5), solutions=arc)
+    assert arc.chi2[0] == st.best_chi2 and np.array_equal(arc.genes[0], st.best_genes)
+    assert arc.chi2 == sorted(arc.chi2) and len(arc.chi2) == 8
+    for i in range(8):
+        for j in range(i + 1, 8):
+            assert np.max(np.abs(arc.genes[i] - arc.genes[j])) > 0.05
