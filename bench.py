@@ -282,7 +282,7 @@ CNN_STEP_FLOP_PER_SAMPLE = 3 * CNN_FWD_FLOP - 2 * 256 * 10 * 64
 
 def _success(best, chi, chi_true, truth, n_ep):
     """Shares of fits meeting: the paper's criterion delta chi^2 / nu < 1 (nu = n_ep - 6, Section
-    4.1), delta chi^2 <= 1, and the strict one (paper's criterion and every parameter within 10%:
+    4.2), delta chi^2 <= 1, and the strict one (paper's criterion and every parameter within 10%:
     t0 relative to tE, alpha relative to 2 pi, the others relative to their own value)."""
     d = chi - chi_true
     da = np.abs((best[:, 3] - truth[:, 3] + np.pi) % (2 * np.pi) - np.pi)
