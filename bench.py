@@ -78,8 +78,9 @@ def whole_job_rate(world, units_per_rank, step_ms):
 
 def sample_clocks_start(device_index):
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv", "w")
+        import tempfile
+
+        f = tempfile.NamedTemporaryFile("w", prefix="sblm_clocks_", suffix=".csv", delete=False)
         p = subprocess.Popen(
             ["nvidia-smi", "-i", str(device_index),
              "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
