@@ -77,10 +77,10 @@ def whole_job_rate(world, units_per_rank, step_ms):
 
 
 def sample_clocks_start(device_index):
-    try:
-        import tempfile
+    import tempfile
 
-        f = tempfile.NamedTemporaryFile("w", prefix="sblm_clocks_", suffix=".csv", delete=False)
+    f = tempfile.NamedTemporaryFile("w", prefix="sblm_clocks_", suffix=".csv", delete=False)
+    try:
         p = subprocess.Popen(
             ["nvidia-smi", "-i", str(device_index),
              "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
@@ -90,6 +90,8 @@ def sample_clocks_start(device_index):
             stdout=f, stderr=subprocess.DEVNULL)
         return p, f
     except (OSError, FileNotFoundError):
+        f.close()
+        os.unlink(f.name)
         return None, None
 
 
