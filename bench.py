@@ -590,10 +590,11 @@ def cpu_baseline_all_cores(sw, flux, sigma, one_core_rate, seconds):
     per = -(-rows // (4 * n))  # about four tasks per process
     jobs = [(sw.theta[k : min(rows, k + per)], sw.t, flux, sigma) for k in range(0, rows, per)]
     ctx = mp.get_context("spawn")
-    with ctx.Pool(n) as pool:
-        pool.map(_oracle_rows, [(sw.theta[:1], sw.t[:4], flux[:4], sigma[:4])] * n)  # imports, outside the timing
+    with ctx.Pool(n) as pool:  # leaving the block terminates the workers, also after a timeout
+        warm = [(sw.theta[:1], sw.t[:4], flux[:4], sigma[:4])] * n
+        pool.map_async(_oracle_rows, warm).get(timeout=300)  # imports, outside the timing
         t0 = time.perf_counter()
-        done = sum(pool.map(_oracle_rows, jobs))
+        done = sum(pool.map_async(_oracle_rows, jobs).get(timeout=max(120.0, 10 * seconds)))
         wall = time.perf_counter() - t0
     t_ops = oracle_operator_seconds()
     per_mag = wall / (done * N_EP) + t_ops / (N_CAND * N_EP)
