@@ -213,7 +213,10 @@ sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t n_pop, int
  *   that device current); make that first call before any stream capture;
  * - every call shares the one array, which keeps the last call's contents (nothing in it has to
  *   start at zero), so calls that overlap on the GPU (other streams, other host threads on the
- *   same device) race: order them on one stream or synchronise between them.
+ *   same device) race: order them on one stream or synchronise between them;
+ * - the looked-up address is cached per device for the life of the process and does not
+ *   survive cudaDeviceReset of that device: after such a reset, do not call this entry point
+ *   again in the same process.
  */
 sblm_status sblm_ea_generation_noalloc(double* P, const double* chi2, int32_t n_pop, int32_t n_par,
                                        const sblm_ea_params* params, uint64_t stream_id,
@@ -295,6 +298,39 @@ typedef struct {
     double rel_tol;          /* parameter tolerance, > 0 (0.1 in the paper) */
     int32_t* first_gen;      /* [n_lc] out: first generation with a matching row, -1 if none */
 } sblm_batch_monitor;
+
+/*
+ * Several solutions per lightcurve (sblm_fit_batch_archived). Section 3.1 obtains multiple
+ * solutions of a problem by keeping the explored phenotypes that meet a fitness criterion, and
+ * Appendix A's EA returns every population. The fitter keeps, per lightcurve, the `size` fittest
+ * mutually distinct solutions among the rows it evaluates: two rows are the same solution when
+ * every encoded gene differs by at most `radius`. Each generation the `top` fittest rows of every
+ * population (all rows when top = 0) are offered in rank order: a row that matches an archived
+ * solution replaces it when its chi^2 is lower (the archive then drops the entries that now match
+ * it) and is dropped otherwise; a new solution enters while there is room, or in place of the
+ * least fit one when it is fitter; rows with a non-finite chi^2 are never archived. Entries are
+ * kept sorted by chi^2 (ties in arrival order), so the first is the EA's best (before the amoeba
+ * polish, which only refines the returned best).
+ */
+typedef struct {
+    int32_t size;     /* solutions kept per lightcurve, 1..64 */
+    int32_t top;      /* rows offered per population and generation (0: all) */
+    double radius;    /* distinctness radius in the encoded genes (in [0, 1]), > 0 */
+    double* theta;    /* [n_lc * size * 6] out: (t0, tE, u0, alpha, d, q); unused entries NaN */
+    double* chi2;     /* [n_lc * size] out: their chi^2 (unused: NaN) */
+    int32_t* count;   /* [n_lc] out: solutions kept */
+} sblm_batch_archive;
+
+/*
+ * sblm_fit_batch_tuned plus the solution archive above (archive must not be NULL; its arrays follow
+ * the pointer rules of the other arguments and are written when the call returns). With FP64 the
+ * archive equals what offering each generation's ranked population to the archive rule gives.
+ */
+sblm_status sblm_fit_batch_archived(const double* t, const double* flux, const double* sigma,
+                                    const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                    const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                    const sblm_batch_archive* archive, double* best_theta, double* best_chi2,
+                                    void* stream);
 
 /*
  * chi^2 of the blended model of Section 4.4 (Eq. blend), A_obs = f A + (1 - f), for each

@@ -179,6 +179,16 @@ sblm_status sblm_fit_batch_monitored(const double* t, const double* flux, const 
                                      const sblm_batch_monitor* monitor, double* best_theta,
                                      double* best_chi2, void* stream);
 
+/*
+ * Diagnostic of the tensor-core kernels' bounded waits (no counterpart in the paper): launches one
+ * block whose wait on an mbarrier that nothing ever arrives on gives up after `polls` polls
+ * (1 <= polls <= 2^20; each poll is one bounded mbarrier.try_wait), sets the device flag that a
+ * tensor-core tile sets when it gives up, and maps it to a status exactly as the sblm_cnn_* calls
+ * do. Expected result: SBLM_ETIMEOUT, with the flag cleared so that the next call starts clean.
+ * No tensor memory is allocated and no MMA is issued. Synchronises `stream`.
+ */
+sblm_status sblm_cnn_selftest_timeout(int32_t polls, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,8 +49,9 @@ struct BatchArgs {
     int n2;            // power of two >= n_pop
     double* P;         // per block: 2 x n_pop x 6
     uint64_t* keys;    // per block: n_pop x 6
-    Deferred* queue;   // per block: qcap entries
+    Deferred* queue;   // MIXED, per block: qcap entries
     unsigned qcap;
+    double* term;      // MIXED, per block: n_pop x max_ep chi^2 terms (row per candidate)
     unsigned* next;    // work counter
     double* best_theta;
     double* best_chi2;
@@ -76,7 +77,76 @@ struct BatchArgs {
     double mon_tol;
     int* mon_first;           // [n_lc] first generation with a matching row, -1 if none
     double* f_scr;            // blend with monitor: per block n_pop profiled f
+    // solution archive (arc_size 0: off)
+    int arc_size;
+    int arc_top;              // rows offered per population and generation
+    double arc_radius;
+    double* arc_genes;        // [n_lc][arc_size][6] genes of the archived solutions
+    double* arc_theta;        // [n_lc][arc_size][6] out
+    double* arc_chi2;         // [n_lc][arc_size] out
+    int* arc_count;           // [n_lc] out
 };
+
+// two encoded solutions are the same when every gene differs by at most r
+__device__ __forceinline__ bool archive_same(const double* a, const double* b, double r) {
+    bool s = true;
+    for (int j = 0; j < SBLM_NPAR; ++j) s &= fabs(a[j] - b[j]) <= r;
+    return s;
+}
+
+// stable insertion sort of the archive by chi^2
+__device__ void archive_sort(double* g, double* c, int n) {
+    for (int i = 1; i < n; ++i) {
+        const double ci = c[i];
+        double gi[SBLM_NPAR];
+        for (int j = 0; j < SBLM_NPAR; ++j) gi[j] = g[i * SBLM_NPAR + j];
+        int k = i;
+        for (; k > 0 && c[k - 1] > ci; --k) {
+            c[k] = c[k - 1];
+            for (int j = 0; j < SBLM_NPAR; ++j) g[k * SBLM_NPAR + j] = g[(k - 1) * SBLM_NPAR + j];
+        }
+        c[k] = ci;
+        for (int j = 0; j < SBLM_NPAR; ++j) g[k * SBLM_NPAR + j] = gi[j];
+    }
+}
+
+// Offer one evaluated row (genes x, chi^2 v) to the archive of `size` entries holding *n (one
+// thread): the rule of sblm_batch_archive in include/sblm.h
+__device__ __noinline__ void archive_offer(double* g, double* c, int* n, int size, double r, const double* x,
+                                           double v) {
+    if (!isfinite(v)) return;
+    for (int k = 0; k < *n; ++k) {
+        if (!archive_same(g + k * SBLM_NPAR, x, r)) continue;
+        if (!(v < c[k])) return;
+        double xk[SBLM_NPAR];
+        for (int j = 0; j < SBLM_NPAR; ++j) xk[j] = g[k * SBLM_NPAR + j] = x[j];
+        c[k] = v;
+        // drop the entries that now match entry k (it is the fitter of each such pair)
+        int w = 0;
+        for (int i = 0; i < *n; ++i) {
+            if (i != k && archive_same(g + i * SBLM_NPAR, xk, r)) continue;
+            if (w != i) {
+                c[w] = c[i];
+                for (int j = 0; j < SBLM_NPAR; ++j) g[w * SBLM_NPAR + j] = g[i * SBLM_NPAR + j];
+            }
+            ++w;
+        }
+        *n = w;
+        archive_sort(g, c, *n);
+        return;
+    }
+    int slot;
+    if (*n < size) {
+        slot = (*n)++;
+    } else if (v < c[*n - 1]) {
+        slot = *n - 1;
+    } else {
+        return;
+    }
+    c[slot] = v;
+    for (int j = 0; j < SBLM_NPAR; ++j) g[slot * SBLM_NPAR + j] = x[j];
+    archive_sort(g, c, *n);
+}
 
 // Section 4.2's strict test of one evaluated row (genes g) against the reference row: every
 // parameter within tol (t0 relative to the reference tE, alpha as a wrapped difference relative
@@ -130,10 +200,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
     __shared__ double s_pmut;
     __shared__ unsigned s_qcount;
     __shared__ int s_first;
+    __shared__ int s_arc_n;
 
     const int n_isl = a.n_isl;
     uint64_t* keys = a.keys + (size_t)blockIdx.x * n_pop * n_par;
-    Deferred* queue = a.queue + (size_t)blockIdx.x * a.qcap;
+    DeferSink sink{};
+    if (MODE == SBLM_MIXED) {
+        sink.queue = a.queue + (size_t)blockIdx.x * a.qcap;
+        sink.queue_count = &s_qcount;
+        sink.queue_cap = a.qcap;
+    }
+    double* const term_blk = MODE == SBLM_MIXED ? a.term + (size_t)blockIdx.x * n_pop * a.max_ep : nullptr;
     const int m = n_pop * n_par;
     double* const Pi = a.P + (size_t)blockIdx.x * n_isl * 2 * m;  // island i: rows Pi + i 2m (two buffers)
     sblm_ea_state* const st_g = a.isl_state + (size_t)blockIdx.x * n_isl;
@@ -177,7 +254,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0) s_first = -1;
+        if (threadIdx.x == 0) {
+            s_first = -1;
+            s_arc_n = 0;
+        }
         __syncthreads();
 
         const int group = threadIdx.x / G, g = threadIdx.x % G;
@@ -203,22 +283,31 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                     const Cand k = group_candidate<true>(Pc, a.b, cand, valid, G);
                     double* A_row =
                         (a.blend && valid) ? a.A_scr + ((size_t)blockIdx.x * n_pop + cand) * a.max_ep : nullptr;
-                    double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, A_row, nullptr, queue,
-                                                            &s_qcount, a.qcap);
+                    double* term_row = (MODE == SBLM_MIXED && valid) ? term_blk + (size_t)cand * a.max_ep : nullptr;
+                    double chi = eval_run<MODE, true, true>(k, valid, cand, e0, e1, seg, view, A_row, nullptr, sink,
+                                                            term_row);
                     for (int off = G / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
                     if (g == 0 && valid) s_chi[cand] = chi;
                 }
                 __syncthreads();
-                if constexpr (MODE == SBLM_MIXED) {  // the block's queued epochs, in FP64
+                if constexpr (MODE == SBLM_MIXED) {
+                    // the block's queued epochs, in FP64 from the FP64 data, each term to its place
+                    // in the candidate's term row; then each candidate's row summed in a fixed order
                     const unsigned n = min(s_qcount, a.qcap);
                     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-                        const Deferred q = queue[i];
+                        const Deferred q = sink.queue[i];
                         const Cand k = candidate<true>(Pc, a.b, q.c);
-                        const float4 ep = view.s_ep[q.e];
                         double* A_rq = a.blend ? a.A_scr + ((size_t)blockIdx.x * n_pop + q.c) * a.max_ep : nullptr;
-                        const double term = resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w,
-                                                         A_rq, nullptr, q.e, true);
-                        atomicAdd(&s_chi[q.c], term);
+                        const int64_t ge = e_begin + q.e;
+                        term_blk[(size_t)q.c * a.max_ep + q.e] = resolve_fp64(
+                            q.z, q.why, &k, a.t[ge], a.flux[ge], 1.0 / a.sigma[ge], A_rq, nullptr, q.e, true);
+                    }
+                    __syncthreads();
+                    for (int base = 0; base < n_pop; base += per_pass) {
+                        const int cand = base + group;
+                        const double* row = term_blk + (size_t)min(cand, n_pop - 1) * a.max_ep;
+                        const double chi = term_row_sum(row, n_ep, g, G, cand < n_pop);
+                        if (g == 0 && cand < n_pop) s_chi[cand] = chi;
                     }
                     __syncthreads();
                 }
@@ -266,6 +355,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
                 }
                 // ranking, archive, stagnation
                 block_rank(s_chi, n_pop, a.n2, s_key, s_idx);
+                if (a.arc_size > 0 && threadIdx.x == 0) {  // offers in rank order, fittest first
+                    double* ag = a.arc_genes + (size_t)lc * a.arc_size * SBLM_NPAR;
+                    double* ac = a.arc_chi2 + (size_t)lc * a.arc_size;
+                    const int top = a.arc_top > 0 ? min(a.arc_top, n_pop) : n_pop;
+                    int n = s_arc_n;
+                    for (int i = 0; i < top; ++i)
+                        archive_offer(ag, ac, &n, a.arc_size, a.arc_radius, Pc + (size_t)s_idx[i] * n_par, s_key[i]);
+                    s_arc_n = n;
+                }
                 if (threadIdx.x == 0) {
                     double p_used = 0.0;
                     s_restart = block_bookkeeping(c, gen, s_key[0], Pc + (size_t)s_idx[0] * n_par, s_state, produce,
@@ -322,6 +420,20 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
             th[5] = exp10(av[5]);
             a.best_chi2[lc] = s_state.best_chi2;
             if (a.mon_first) a.mon_first[lc] = s_first;
+            if (a.arc_size > 0) {
+                const double* ag = a.arc_genes + (size_t)lc * a.arc_size * SBLM_NPAR;
+                double* at = a.arc_theta + (size_t)lc * a.arc_size * SBLM_NPAR;
+                double* ac = a.arc_chi2 + (size_t)lc * a.arc_size;
+                for (int k = 0; k < a.arc_size; ++k) {
+                    double av[SBLM_NPAR];
+                    for (int j = 0; j < SBLM_NPAR; ++j)
+                        av[j] = k < s_arc_n ? a.b.lo[j] + (a.b.hi[j] - a.b.lo[j]) * ag[k * SBLM_NPAR + j] : NAN;
+                    for (int j = 0; j < 5; ++j) at[k * SBLM_NPAR + j] = av[j];
+                    at[k * SBLM_NPAR + 5] = k < s_arc_n ? exp10(av[5]) : NAN;
+                    if (k >= s_arc_n) ac[k] = NAN;
+                }
+                a.arc_count[lc] = s_arc_n;
+            }
             for (int j = 0; j < SBLM_NPAR; ++j) a.best_genes[(size_t)lc * SBLM_NPAR + j] = s_state.best_genes[j];
         }
         __syncthreads();
@@ -343,7 +455,7 @@ template <int MODE>
 cudaError_t launch_batch_mode(const BatchArgs& a, int blocks, int threads, size_t smem, cudaStream_t s,
                               bool attr_only) {
     auto kern = batch_fit_kernel<MODE>;
-    if (attr_only) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr_only) return raise_smem_limit((const void*)kern, smem);
     kern<<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -381,7 +493,8 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
                     const sblm_bounds* bounds, const sblm_ea_params* params, const sblm_batch_tuning* tuning,
                     const double* seed_genes, int n_seed, double* best_theta, double* best_chi2, Staging& st,
                     int* i_th, int* i_c, Prepared* out, size_t extra_bytes = 0, int* k_extra = nullptr,
-                    const sblm_batch_monitor* mon = nullptr, int* i_mon = nullptr) {
+                    const sblm_batch_monitor* mon = nullptr, int* i_mon = nullptr,
+                    const sblm_batch_archive* arc = nullptr, int* i_arc = nullptr) {
     if (!params) return fail(SBLM_EINVAL, "params is NULL");
     const int mode = params->precision & ~SBLM_BLEND;
     const bool blend = (params->precision & SBLM_BLEND) != 0;
@@ -441,8 +554,13 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     // per block: room for a quarter of a generation's epochs (a population gathered on a
     // caustic-crossing model defers many); epochs past this are re-solved in place, one divergent
     // lane at a time, so the size is a speed choice only
+    // per block: room for a quarter of a generation's epochs (a population gathered on a
+    // caustic-crossing model defers many), within 2^26 entries (~3 GB) over all blocks; epochs past
+    // this are re-solved in place, one divergent lane at a time, so the size is a speed choice only
     const unsigned qcap =
-        mode == SBLM_MIXED ? (unsigned)std::min<long>(std::max<long>((long)c.n_pop * max_ep / 4, 4096), 65536) : 0;
+        mode == SBLM_MIXED
+            ? (unsigned)std::max<long>(4096, std::min<long>((long)c.n_pop * max_ep / 4, (1L << 26) / blocks))
+            : 0;
     const int k_order = st.scratch(sizeof(int) * n_lc);
     const int n_isl = std::max(1, params->n_islands);
     if (n_isl > kMaxIslands) return fail(SBLM_EINVAL, "n_islands=%d outside [1, %d]", n_isl, kMaxIslands);
@@ -451,13 +569,14 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     const int k_ie = st.scratch(n_isl > 1 ? sizeof(double) * SBLM_NPAR * (size_t)blocks * n_isl : 0);
     const int k_keys = st.scratch(sizeof(uint64_t) * (size_t)c.n_pop * SBLM_NPAR * blocks);
     const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
+    const int k_term = st.scratch(mode == SBLM_MIXED ? sizeof(double) * (size_t)c.n_pop * max_ep * blocks : 0);
     const int k_next = st.scratch(sizeof(unsigned));
     const int k_genes = st.scratch(sizeof(double) * SBLM_NPAR * (size_t)n_lc);
     const int k_A = st.scratch(blend ? sizeof(double) * (size_t)blocks * c.n_pop * max_ep : 0);
     const int polish_blocks = std::min(n_lc, 2 * sms);
     const int k_pA = st.scratch(blend && params->polish_fev > 0 ? sizeof(double) * (size_t)polish_blocks * max_ep : 0);
-    const unsigned pq = params->polish_fev > 0 ? polish_queue_capacity(mode, max_ep) : 0;
-    const int k_pq = st.scratch(deferred_entry_bytes() * (size_t)pq * polish_blocks);
+    const PolishMixed pmx = polish_mixed_layout(max_ep);
+    const int k_pq = st.scratch(mode == SBLM_MIXED && params->polish_fev > 0 ? pmx.block_bytes * polish_blocks : 0);
     if (params->polish_fev > 0 && polish_smem_bytes(mode, max_ep) > kPolishSmemBudget)
         return fail(SBLM_EINVAL, "the amoeba polish stages at most %zu bytes of epochs (longest lightcurve %d)",
                     kPolishSmemBudget, max_ep);
@@ -478,6 +597,17 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
         if (mon->f_ref) SBLM_TRY(st.arg(mon->f_ref, sizeof(double) * (size_t)n_lc, true, false, &i_mf));
         SBLM_TRY(st.arg(mon->first_gen, sizeof(int32_t) * (size_t)n_lc, false, true, i_mon));
         if (blend) k_f = st.scratch(sizeof(double) * (size_t)blocks * c.n_pop);
+    }
+    int k_ag = -1;
+    if (arc) {
+        if (arc->size < 1 || arc->size > 64) return fail(SBLM_EINVAL, "archive size must be in [1, 64]");
+        if (arc->top < 0) return fail(SBLM_EINVAL, "archive top must be >= 0");
+        if (!(arc->radius > 0.0) || !std::isfinite(arc->radius)) return fail(SBLM_EINVAL, "archive radius must be > 0");
+        if (!arc->theta || !arc->chi2 || !arc->count) return fail(SBLM_EINVAL, "the archive needs theta, chi2 and count");
+        SBLM_TRY(st.arg(arc->theta, sizeof(double) * SBLM_NPAR * (size_t)n_lc * arc->size, false, true, &i_arc[0]));
+        SBLM_TRY(st.arg(arc->chi2, sizeof(double) * (size_t)n_lc * arc->size, false, true, &i_arc[1]));
+        SBLM_TRY(st.arg(arc->count, sizeof(int32_t) * (size_t)n_lc, false, true, &i_arc[2]));
+        k_ag = st.scratch(sizeof(double) * SBLM_NPAR * (size_t)n_lc * arc->size);
     }
     SBLM_TRY(st.begin());
     // longest first (stable): the classic longest-processing-time order for the work queue
@@ -503,6 +633,7 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.keys = static_cast<uint64_t*>(st.scratch_ptr(k_keys));
     a.queue = static_cast<Deferred*>(st.scratch_ptr(k_q));
     a.qcap = qcap;
+    a.term = static_cast<double*>(st.scratch_ptr(k_term));
     a.next = static_cast<unsigned*>(st.scratch_ptr(k_next));
     a.best_theta = static_cast<double*>(st.dev(*i_th));
     a.best_chi2 = static_cast<double*>(st.dev(*i_c));
@@ -526,6 +657,15 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
         a.mon_first = static_cast<int*>(st.dev(*i_mon));
         a.f_scr = k_f >= 0 ? static_cast<double*>(st.scratch_ptr(k_f)) : nullptr;
     }
+    if (arc) {
+        a.arc_size = arc->size;
+        a.arc_top = arc->top;
+        a.arc_radius = arc->radius;
+        a.arc_genes = static_cast<double*>(st.scratch_ptr(k_ag));
+        a.arc_theta = static_cast<double*>(st.dev(i_arc[0]));
+        a.arc_chi2 = static_cast<double*>(st.dev(i_arc[1]));
+        a.arc_count = static_cast<int*>(st.dev(i_arc[2]));
+    }
     out->a = a;
     PolishArgs pa{};
     pa.t = a.t;
@@ -541,8 +681,8 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     pa.g_out = a.best_genes;
     pa.c_out = a.best_chi2;
     pa.maxfev = params->polish_fev;
-    pa.queue = static_cast<Deferred*>(st.scratch_ptr(k_pq));
-    pa.qcap = pq;
+    pa.mixed = st.scratch_ptr(k_pq);
+    pa.mx = pmx;
     pa.blend = blend ? 1 : 0;
     pa.f_min = SBLM_BLEND_F_MIN;
     pa.A_scr = blend && params->polish_fev > 0 ? static_cast<double*>(st.scratch_ptr(k_pA)) : nullptr;
@@ -630,6 +770,25 @@ extern "C" sblm_status sblm_fit_batch_seeded(const double* t, const double* flux
     Prepared p;
     SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, n_seed > 0 ? seed_genes : nullptr, n_seed,
                      best_theta, best_chi2, st, &i_th, &i_c, &p));
+    SBLM_TRY(run_graph(p, s));
+    SBLM_TRY(st.end());
+    SBLM_CUDA(cudaStreamSynchronize(s));
+    return SBLM_OK;
+}
+
+extern "C" sblm_status sblm_fit_batch_archived(const double* t, const double* flux, const double* sigma,
+                                               const int64_t* offsets, int32_t n_lc, const sblm_bounds* bounds,
+                                               const sblm_ea_params* params, const sblm_batch_tuning* tuning,
+                                               const sblm_batch_archive* archive, double* best_theta,
+                                               double* best_chi2, void* stream) {
+    if (!archive) return fail(SBLM_EINVAL, "archive is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    int i_th, i_c, i_arc[3];
+    Prepared p;
+    SBLM_TRY(prepare(t, flux, sigma, offsets, n_lc, bounds, params, tuning, nullptr, 0, best_theta, best_chi2, st,
+                     &i_th, &i_c, &p, 0, nullptr, nullptr, nullptr, archive, i_arc));
     SBLM_TRY(run_graph(p, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));

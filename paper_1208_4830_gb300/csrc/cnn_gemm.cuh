@@ -17,7 +17,11 @@
 // descriptors' leading-dimension offset is the step between core matrices along K, the
 // stride-dimension offset the step between them along M or N. Two stages: the global loads of the next K-tile overlap the MMAs of the
 // current one, each stage released by an mbarrier that tcgen05.commit arrives on. Every wait is
-// bounded; a wait that gives up sets g_tc_timeout, which the host reads after the call.
+// bounded; a wait that gives up sets g_tc_timeout, which the host reads after the call. The
+// give-up decision is made block-wide (__syncthreads_and) before any barrier or .sync.aligned
+// instruction that depends on it: after it no further MMA is issued, the epilogue is skipped, and
+// the block waits for the MMAs already issued (one more commit on a drain barrier) before it
+// frees its tensor memory.
 // The accumulators leave tensor memory through a shared-memory staging tile, so that each warp's
 // epilogue covers one whole 64-column row (coalesced). Two tiles are fetched ahead in registers.
 // Epilogue functors receive two adjacent columns (m, n), (m, n + 1) per call.
@@ -74,8 +78,8 @@ __host__ __device__ constexpr uint32_t idesc_f16(bool a_mn, bool b_mn) {
            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    for (int it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, int limit = kWaitLimit) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -129,6 +133,7 @@ template <bool AK, bool BKM, class LA, class LB, class EP>
 __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(LA la, LB lb, EP ep, int M, int N, int K, int tps) {
     extern __shared__ unsigned char dsmem[];
     __shared__ __align__(8) uint64_t mbar[kStages];
+    __shared__ __align__(8) uint64_t mbar_drain;  // completes once every MMA issued so far has (give-up path)
     __shared__ uint32_t s_tmem;
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
     unsigned char* sA[kStages] = {base, base + kTileA + kTileB};
@@ -140,6 +145,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(LA la, LB lb, EP ep,
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_drain)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -178,9 +184,9 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(LA la, LB lb, EP ep,
         tile_store<BN>(sB[st], rb[st]);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        ok = __syncthreads_and(ok) != 0;  // one decision for the block: no MMA is issued after a give-up
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
+        if (tid == 0 && ok) {
             const uint32_t a0 = smem_u32(sA[st]), b0 = smem_u32(sB[st]);
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(LA la, LB lb, EP ep,
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar[st])));
         }
-        pending[st] = true;
+        pending[st] = ok;
         if (t + 2 < t_end) {
             tile_fetch<AK, BM>(la, m0, (t + 2) * BK, ra[st]);
             tile_fetch<BKM, BN>(lb, n0, (t + 2) * BK, rb[st]);
@@ -210,7 +216,18 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(LA la, LB lb, EP ep,
             ok = mbar_wait(smem_u32(&mbar[s]), parity[s]) && ok;
             parity[s] ^= 1u;
         }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) {
+        // a wait gave up: the MMAs issued so far may still be running. Track them all with one more
+        // commit and wait for it (bounded again) before the tensor memory is freed
+        if (tid == 0)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar_drain)));
+        mbar_wait(smem_u32(&mbar_drain), 0u);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
     if (ok && t_end > t_begin) {
         float* sE = reinterpret_cast<float*>(base);  // the tile ring is free: every MMA has completed
         const int q = warp & 3, half = warp >> 2;

@@ -142,15 +142,9 @@ cudaError_t launch_rank(const EAConst& c, int gen, const double* chi2, const dou
     int n2 = 1;
     while (n2 < c.n_pop) n2 <<= 1;
     const size_t smem = (size_t)n2 * (sizeof(double) + sizeof(int));
-    static size_t granted[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    // opt in beyond 48 KB (with the kernel's static shared memory)
+    cudaError_t e = raise_smem_limit((const void*)rank_kernel, smem);
     if (e != cudaSuccess) return e;
-    if (smem > granted[dev & 63]) {  // opt in beyond 48 KB (with the kernel's static shared memory)
-        e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        granted[dev & 63] = smem;
-    }
     rank_kernel<<<1, kRankThreads, smem, s>>>(c, gen, chi2, P, state, order, ctrl, keys, trace_row, produce ? 1 : 0);
     return cudaGetLastError();
 }
@@ -228,6 +222,7 @@ constexpr int kNoAllocMaxElems = 32768;   // largest N_pop * N_par
 constexpr size_t kNoAllocOrder = 0;                                              // int32 [N_pop]
 constexpr size_t kNoAllocCtrl = kNoAllocOrder + sizeof(int) * kNoAllocMaxPop;    // EACtrl
 constexpr size_t kNoAllocKeys = kNoAllocCtrl + 256;                              // uint64 [M]
+static_assert(sizeof(EACtrl) <= 256, "the control word's slot in the fixed scratch is 256 bytes");
 constexpr size_t kNoAllocNext = kNoAllocKeys + sizeof(uint64_t) * kNoAllocMaxElems;  // double [M]
 constexpr size_t kNoAllocBytes = kNoAllocNext + sizeof(double) * kNoAllocMaxElems;   // 544 KiB + 256 B
 

@@ -33,12 +33,13 @@ void put(std::vector<unsigned char>& k, const V& v) {
 }
 
 std::vector<unsigned char> fit_graph_key(const EAConst& c, const ForwardArgs& fa, int n_gen, const double* tr,
-                                         const double* th, const double* chi, const double* P0, int polish_fev) {
+                                         const double* th, const double* chi, const double* P0, int polish_fev,
+                                         const void* polish_mixed) {
     std::vector<unsigned char> k;
     put(k, c.n_pop), put(k, c.n_par), put(k, c.n_tourn), put(k, c.stag_window), put(k, c.restart_after);
     put(k, c.p_mut0), put(k, c.stag_rel), put(k, c.seed), put(k, c.stream);
     put(k, fa.t), put(k, fa.flux), put(k, fa.sigma), put(k, fa.n_ep), put(k, fa.n_cand), put(k, fa.mode);
-    put(k, fa.G), put(k, fa.chi2_out), put(k, fa.queue), put(k, fa.queue_count), put(k, fa.queue_cap);
+    put(k, fa.G), put(k, fa.chi2_out), put(k, fa.mixed), put(k, polish_mixed);
     for (int j = 0; j < SBLM_NPAR; ++j) put(k, fa.bounds.lo[j]), put(k, fa.bounds.hi[j]);
     put(k, n_gen), put(k, tr), put(k, th), put(k, chi), put(k, P0);
     put(k, polish_fev);
@@ -106,8 +107,11 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     const int k_ctrl = st.scratch(sizeof(EACtrl));
     const int k_keys = st.scratch(sizeof(uint64_t) * m);
     const int k_state = st.scratch(sizeof(sblm_ea_state));
-    const unsigned qcap = params->precision == SBLM_MIXED ? mixed_queue_capacity(n_pop, n_ep) : 0;
-    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
+    const int G = choose_group(n_pop, n_ep);
+    const bool mixed = params->precision == SBLM_MIXED;
+    const int k_mx = st.scratch(mixed ? mixed_scratch_bytes(n_pop, n_ep, true) : 0);
+    const PolishMixed pmx = polish_mixed_layout(n_ep);
+    const int k_pmx = st.scratch(mixed && polish_fev > 0 ? pmx.block_bytes : 0);
     SBLM_TRY(st.begin());
 
     double* P[2] = {static_cast<double*>(st.scratch_ptr(k_P0)), static_cast<double*>(st.scratch_ptr(k_P1))};
@@ -128,10 +132,9 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
     fa.n_ep = n_ep;
     fa.chi2_out = chi;
     fa.mode = params->precision;
-    fa.G = choose_group(n_pop, n_ep);
-    fa.queue = st.scratch_ptr(k_q);
-    fa.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
-    fa.queue_cap = qcap;
+    fa.G = G;
+    fa.mixed = st.scratch_ptr(k_mx);
+    void* polish_mixed = st.scratch_ptr(k_pmx);
 
     double* th_out = static_cast<double*>(st.dev(i_th));
     double* chi_out = static_cast<double*>(st.dev(i_c));
@@ -169,8 +172,8 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
             pa.g_out = state->best_genes;
             pa.c_out = &state->best_chi2;
             pa.maxfev = polish_fev;
-            pa.queue = static_cast<Deferred*>(fa.queue);
-            pa.qcap = fa.queue_cap;
+            pa.mixed = polish_mixed;
+            pa.mx = pmx;
             e = launch_polish(fa.mode, pa, 1, n_ep, q);
         }
         if (e == cudaSuccess) {
@@ -179,7 +182,7 @@ extern "C" sblm_status sblm_fit(const double* t, const double* flux, const doubl
         }
         return e;
     };
-    SBLM_TRY(run_cached_graph(fit_graph_key(c, fa, n_gen, tr, th_out, chi_out, P[0], polish_fev), enqueue, s));
+    SBLM_TRY(run_cached_graph(fit_graph_key(c, fa, n_gen, tr, th_out, chi_out, P[0], polish_fev, polish_mixed), enqueue, s));
     SBLM_TRY(st.end());
     SBLM_CUDA(cudaStreamSynchronize(s));
     return SBLM_OK;

@@ -19,9 +19,9 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// MIXED, second pass: the queued epochs in full warps over the whole GPU. Each chi^2 term is
-// added atomically to its candidate's FP32 partial sum, so the summation order of these terms
-// (and the last bits of a MIXED chi^2) can vary from run to run.
+// MIXED, second pass: the queued epochs in full warps over the whole GPU. Each chi^2 term goes to
+// its (candidate, epoch) place in the dense term array (no atomics), so the sums of the third pass
+// do not depend on the order in which the queue was filled.
 template <bool CHI2, bool FROM_GENES>
 __global__ void __launch_bounds__(256) resolve_kernel(const double* __restrict__ src, Bounds bounds,
                                                       const double* __restrict__ t,
@@ -30,17 +30,26 @@ __global__ void __launch_bounds__(256) resolve_kernel(const double* __restrict__
                                                       const Deferred* __restrict__ queue,
                                                       const unsigned* __restrict__ count, unsigned cap,
                                                       double* __restrict__ A_out, uint8_t* __restrict__ flags,
-                                                      double* __restrict__ chi2_out) {
+                                                      double* __restrict__ term) {
     const unsigned n = min(*count, cap);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Deferred q = queue[i];
         const Cand k = candidate<FROM_GENES>(src, bounds, q.c);
         const double fe = CHI2 ? flux[q.e] : 0.0;
         const double we = CHI2 ? 1.0 / sigma[q.e] : 0.0;
-        const double term = resolve_fp64(q.z, q.why, &k, t[q.e], fe, we, A_out ? A_out + (size_t)q.c * n_ep : nullptr,
-                                         flags ? flags + (size_t)q.c * n_ep : nullptr, q.e, CHI2);
-        if (CHI2) atomicAdd(&chi2_out[q.c], term);
+        const double tm = resolve_fp64(q.z, q.why, &k, t[q.e], fe, we, A_out ? A_out + (size_t)q.c * n_ep : nullptr,
+                                       flags ? flags + (size_t)q.c * n_ep : nullptr, q.e, CHI2);
+        if (CHI2) term[(size_t)q.c * n_ep + q.e] = tm;
     }
+}
+
+// MIXED, third pass: chi^2 of candidate (warp) c as the sum of its term row in a fixed order
+// (lane l adds epochs l, l + 32, ... in order, then a fixed butterfly)
+__global__ void term_sum_kernel(int n_cand, int n_ep, const double* __restrict__ term, double* __restrict__ chi2_out) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (c >= n_cand) return;  // whole warps leave together
+    const double s = term_row_sum(term + (size_t)c * n_ep, n_ep, lane, 32, true);
+    if (lane == 0) chi2_out[c] = s;
 }
 
 // blended chi^2 of candidate (warp) c from its magnification row: lanes take epochs lane,
@@ -83,9 +92,8 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
                                                          const double* __restrict__ sigma, int n_ep,
                                                          double* __restrict__ A_out,
                                                          uint8_t* __restrict__ flags,
-                                                         double* __restrict__ chi2_out, int G,
-                                                         Deferred* __restrict__ queue,
-                                                         unsigned* __restrict__ queue_count, unsigned queue_cap) {
+                                                         double* __restrict__ chi2_out, int G, DeferSink sink,
+                                                         double* __restrict__ term) {
     extern __shared__ __align__(16) unsigned char smem[];
     const LCView lc = STAGED ? stage_lightcurve<MODE, CHI2>(smem, t, flux, sigma, n_ep)
                              : LCView{t, flux, sigma, nullptr, nullptr, nullptr, nullptr};
@@ -101,9 +109,9 @@ __global__ void __launch_bounds__(kBlock, 2) forward_kernel(const double* __rest
     const Cand k = group_candidate<FROM_GENES>(src, bounds, c, valid, G);
     double* A_row = (A_out && valid) ? A_out + (size_t)c * n_ep : nullptr;
     uint8_t* f_row = (flags && valid) ? flags + (size_t)c * n_ep : nullptr;
-    double chi = eval_run<MODE, CHI2, STAGED>(k, valid, c, e0, e1, seg, lc, A_row, f_row, queue, queue_count,
-                                              queue_cap);
-    if (!CHI2) return;
+    double* term_row = (MODE == SBLM_MIXED && CHI2 && valid) ? term + (size_t)c * n_ep : nullptr;
+    double chi = eval_run<MODE, CHI2, STAGED>(k, valid, c, e0, e1, seg, lc, A_row, f_row, sink, term_row);
+    if (!CHI2 || MODE == SBLM_MIXED) return;  // MIXED: the term rows are summed after the re-solve
     // deterministic reduction over the candidate's G threads
     const int width = min(G, 32);
     for (int off = width / 2; off > 0; off >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, off);
@@ -128,25 +136,31 @@ cudaError_t launch_t(const ForwardArgs& a, cudaStream_t s) {
     const size_t smem = STAGED ? staged_bytes(MODE, CHI2, a.n_ep) : 0;
     // opt in to more than 48 KB (dynamic plus the kernel's static shared memory) once per
     // device and size
-    static size_t granted[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = raise_smem_limit((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    if (smem > granted[dev & 63]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        granted[dev & 63] = smem;
-    }
     const int per_block = kBlock / a.G;
     const int grid = (a.n_cand + per_block - 1) / per_block;
+    DeferSink sink{};
+    MixedLayout ml;
+    double* term = nullptr;
+    if (MODE == SBLM_MIXED) {
+        ml = mixed_layout(a.n_cand, a.n_ep, CHI2);
+        char* m = static_cast<char*>(a.mixed);
+        sink.queue = reinterpret_cast<Deferred*>(m);
+        sink.queue_count = reinterpret_cast<unsigned*>(m + ml.off_count);
+        sink.queue_cap = ml.queue_cap;
+        term = CHI2 ? reinterpret_cast<double*>(m + ml.off_term) : nullptr;
+    }
     kern<<<grid, kBlock, smem, s>>>(a.src, a.bounds, a.n_cand, a.t, a.flux, a.sigma, a.n_ep, a.A_out, a.flags,
-                                    a.chi2_out, a.G, static_cast<Deferred*>(a.queue), a.queue_count, a.queue_cap);
+                                    a.chi2_out, a.G, sink, term);
     e = cudaGetLastError();
-    if (e != cudaSuccess || MODE != SBLM_MIXED || a.queue_cap == 0) return e;
-    const int rgrid = (int)std::min<unsigned>((a.queue_cap + 255) / 256, 152u * 8u);
-    resolve_kernel<CHI2, FROM_GENES><<<rgrid, 256, 0, s>>>(a.src, a.bounds, a.t, a.flux, a.sigma, a.n_ep,
-                                                          static_cast<const Deferred*>(a.queue), a.queue_count,
-                                                          a.queue_cap, a.A_out, a.flags, a.chi2_out);
+    if (e != cudaSuccess || MODE != SBLM_MIXED) return e;
+    const int rgrid = (int)std::min<unsigned>((ml.queue_cap + 255) / 256, 8u * (unsigned)device_sm_count());
+    resolve_kernel<CHI2, FROM_GENES><<<rgrid, 256, 0, s>>>(a.src, a.bounds, a.t, a.flux, a.sigma, a.n_ep, sink.queue,
+                                                          sink.queue_count, ml.queue_cap, a.A_out, a.flags, term);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !CHI2) return e;
+    term_sum_kernel<<<(int)(((long)a.n_cand * 32 + 255) / 256), 256, 0, s>>>(a.n_cand, a.n_ep, term, a.chi2_out);
     return cudaGetLastError();
 }
 
@@ -166,11 +180,11 @@ size_t staged_bytes(int mode, bool chi2, int n_ep) {
 }
 
 int choose_group(int n_cand, int n_ep) {
-    // threads to fill the GPU four times over (152 SMs x 2 blocks x 256 threads is one fill), at
+    // threads to fill the GPU four times over (SMs x 2 blocks x 256 threads is one fill), at
     // least ~4 epochs per thread so warm starts pay off. On the 4096 x 2000 sweep 256 threads per
     // candidate (8 epochs each, a candidate per block) beat 64 threads (31 epochs each) by 8%:
     // more warps hide latency, and a block's warps carry similar work
-    const long target = 152L * 4096;
+    const long target = (long)device_sm_count() * 4096;
     long g = 1;
     while (g * n_cand < target && g < 256) g <<= 1;
     long cap = 1;
@@ -178,17 +192,28 @@ int choose_group(int n_cand, int n_ep) {
     return (int)std::max(1L, std::min(g, cap));
 }
 
-unsigned mixed_queue_capacity(int n_cand, int n_ep) {
-    const long n = (long)n_cand * n_ep / 32;
-    return (unsigned)std::min<long>(std::max<long>(n, 4096), 1L << 24);
+MixedLayout mixed_layout(int n_cand, int n_ep, bool chi2) {
+    MixedLayout l;
+    if (n_cand <= 0 || n_ep <= 0) return l;
+    // a queue entry for one epoch in 32 (0.55% of the sweep's epochs defer, 4.2% of those of the
+    // trajectories aimed at caustics), at least 4096 and at most 2^24 entries (0.9 GB)
+    const long n = (long)n_cand * n_ep;
+    l.queue_cap = (unsigned)std::min<long>(std::max<long>(n / 32, 4096), 1L << 24);
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    l.off_count = up(sizeof(Deferred) * (size_t)l.queue_cap);
+    l.off_term = up(l.off_count + sizeof(unsigned));
+    l.bytes = up(l.off_term + (chi2 ? sizeof(double) * (size_t)n : 0));
+    return l;
 }
 
 size_t deferred_entry_bytes() { return sizeof(Deferred); }
 
 cudaError_t launch_forward(const ForwardArgs& a, cudaStream_t s) {
     if (a.n_cand <= 0 || a.n_ep <= 0) return cudaSuccess;
-    if (a.mode == SBLM_MIXED && a.queue_cap > 0) {
-        cudaError_t e = cudaMemsetAsync(a.queue_count, 0, sizeof(unsigned), s);
+    if (a.mode == SBLM_MIXED) {
+        if (!a.mixed) return cudaErrorInvalidValue;
+        const MixedLayout ml = mixed_layout(a.n_cand, a.n_ep, a.chi2_out != nullptr);
+        cudaError_t e = cudaMemsetAsync(static_cast<char*>(a.mixed) + ml.off_count, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
     }
     const bool chi2 = a.chi2_out != nullptr;
@@ -237,8 +262,8 @@ extern "C" sblm_status sblm_magnification(const double* theta, int32_t n_cand, c
     SBLM_TRY(st.arg(t, sizeof(double) * (size_t)n_ep, true, false, &i_t));
     SBLM_TRY(st.arg(A_out, sizeof(double) * (size_t)n_cand * n_ep, false, true, &i_A));
     SBLM_TRY(st.arg(flags, flags ? (size_t)n_cand * n_ep : 0, false, true, &i_f));
-    const unsigned qcap = precision == SBLM_MIXED ? mixed_queue_capacity(n_cand, n_ep) : 0;
-    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
+    const int G = choose_group(n_cand, n_ep);
+    const int k_mx = st.scratch(precision == SBLM_MIXED ? mixed_scratch_bytes(n_cand, n_ep, false) : 0);
     bool on_dev = true;
     SBLM_TRY(is_device_pointer(theta, &on_dev));
     if (!on_dev) SBLM_TRY(check_theta_host(theta, n_cand));
@@ -253,10 +278,8 @@ extern "C" sblm_status sblm_magnification(const double* theta, int32_t n_cand, c
     a.A_out = static_cast<double*>(st.dev(i_A));
     a.flags = static_cast<uint8_t*>(st.dev(i_f));
     a.mode = precision;
-    a.G = choose_group(n_cand, n_ep);
-    a.queue = st.scratch_ptr(k_q);
-    a.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
-    a.queue_cap = qcap;
+    a.G = G;
+    a.mixed = st.scratch_ptr(k_mx);
     SBLM_CUDA(launch_forward(a, s));
     return st.end();
 }
@@ -281,8 +304,8 @@ static sblm_status chi2_impl(const double* src, bool genes, const Bounds& b, int
     SBLM_TRY(st.arg(flux, sizeof(double) * (size_t)n_ep, true, false, &i_f));
     SBLM_TRY(st.arg(sigma, sizeof(double) * (size_t)n_ep, true, false, &i_s));
     SBLM_TRY(st.arg(chi2_out, sizeof(double) * (size_t)n_cand, false, true, &i_c));
-    const unsigned qcap = precision == SBLM_MIXED ? mixed_queue_capacity(n_cand, n_ep) : 0;
-    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
+    const int G = choose_group(n_cand, n_ep);
+    const int k_mx = st.scratch(precision == SBLM_MIXED ? mixed_scratch_bytes(n_cand, n_ep, true) : 0);
     bool on_dev = true;
     SBLM_TRY(is_device_pointer(src, &on_dev));
     if (!on_dev && !genes) SBLM_TRY(check_theta_host(src, n_cand));
@@ -309,10 +332,8 @@ static sblm_status chi2_impl(const double* src, bool genes, const Bounds& b, int
     a.n_ep = n_ep;
     a.chi2_out = static_cast<double*>(st.dev(i_c));
     a.mode = precision;
-    a.G = choose_group(n_cand, n_ep);
-    a.queue = st.scratch_ptr(k_q);
-    a.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
-    a.queue_cap = qcap;
+    a.G = G;
+    a.mixed = st.scratch_ptr(k_mx);
     SBLM_CUDA(launch_forward(a, s));
     return st.end();
 }
@@ -342,9 +363,9 @@ extern "C" sblm_status sblm_chi2_blend(const double* theta, int32_t n_cand, cons
     SBLM_TRY(st.arg(sigma, sizeof(double) * (size_t)n_ep, true, false, &i_s));
     SBLM_TRY(st.arg(chi2_out, sizeof(double) * (size_t)n_cand, false, true, &i_c));
     SBLM_TRY(st.arg(f_out, f_out ? sizeof(double) * (size_t)n_cand : 0, false, true, &i_fo));
-    const unsigned qcap = precision == SBLM_MIXED ? mixed_queue_capacity(n_cand, n_ep) : 0;
+    const int G = choose_group(n_cand, n_ep);
     const int k_A = st.scratch(sizeof(double) * (size_t)n_cand * n_ep);
-    const int k_q = st.scratch(deferred_entry_bytes() * qcap), k_qc = st.scratch(sizeof(unsigned));
+    const int k_mx = st.scratch(precision == SBLM_MIXED ? mixed_scratch_bytes(n_cand, n_ep, false) : 0);
     bool d = true;
     SBLM_TRY(is_device_pointer(theta, &d));
     if (!d) SBLM_TRY(check_theta_host(theta, n_cand));
@@ -360,10 +381,8 @@ extern "C" sblm_status sblm_chi2_blend(const double* theta, int32_t n_cand, cons
     a.n_ep = n_ep;
     a.A_out = static_cast<double*>(st.scratch_ptr(k_A));
     a.mode = precision;
-    a.G = choose_group(n_cand, n_ep);
-    a.queue = st.scratch_ptr(k_q);
-    a.queue_count = static_cast<unsigned*>(st.scratch_ptr(k_qc));
-    a.queue_cap = qcap;
+    a.G = G;
+    a.mixed = st.scratch_ptr(k_mx);
     if (n_ep > 0) SBLM_CUDA(launch_forward(a, s));
     const int threads = 256, blocks = (int)(((long)n_cand * 32 + threads - 1) / threads);
     blend_kernel<<<blocks, threads, 0, s>>>(a.A_out, static_cast<const double*>(st.dev(i_f)),

@@ -195,6 +195,10 @@ struct EpochOut {
     T min_det_rej;  // smallest |det J| over the rejected roots that nearly solve the lens equation
                     // (relative residual below kSpurious): a pair of images that the arithmetic
                     // failed to converge sits next to the critical curve
+    T min_gap_rej;  // smallest distance, relative to sqrt(1 + |z|^2), between two rejected roots with
+                    // relative residuals below kSpuriousPair: an image pair just born at a fold
+                    // that the iteration left as one near-double root (both roots stop at the
+                    // noise level of the polynomial there)
     int sweeps;  // root-iteration sweeps spent (diagnostics)
     uint8_t flag;
 };
@@ -234,6 +238,8 @@ __device__ __forceinline__ void lens_terms(const Root<T>& r, cx<T> zeta, T d, T 
 
 // roots whose relative lens-equation residual exceeds this are spurious without a polish
 constexpr float kSpurious = 0.05f;
+// rejected roots with residuals below this enter the near-double-root test (min_gap_rej)
+constexpr float kSpuriousPair = 0.25f;
 
 // Spurious-root rejection (Section 2.2: substitution into Eq. (lensing)) and magnification.
 // Each root gets `polish` Newton steps on the lens equation itself,
@@ -380,6 +386,15 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
     for (int i = 0; i < 5; ++i)
         if (!acc[i] && r2[i] <= T(kSpurious) * T(kSpurious)) mdr = fmin(mdr, fabs(det[i]));
     out.min_det_rej = mdr;
+    T mgr = T(INFINITY);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 5; ++j)
+            if (!acc[i] && !acc[j] && r2[i] <= T(kSpuriousPair) * T(kSpuriousPair) &&
+                r2[j] <= T(kSpuriousPair) * T(kSpuriousPair))
+                mgr = fmin(mgr, norm2(root_diff(rp[i], rp[j])) / (T(1) + norm2(rp[i].z)));
+    out.min_gap_rej = sqrt_(mgr);
     out.A = A;
     out.min_det = md;
     out.min_gap = sqrt_(min_gap2);
@@ -514,6 +529,24 @@ __device__ __forceinline__ float diff_ff(float ah, float al, float bh, float bl)
     const float v = s - ah;
     const float e = (ah - (s - v)) + (-bh - v);
     return s + (e + (al - bl));
+}
+
+// MIXED: an epoch solved in FP32 is re-solved in FP64 when an image, or a rejected root that
+// nearly solves the lens equation, has |det J| below kMixedDetTrigger (next to a caustic FP32
+// loses accuracy, and an image pair it failed to converge sits next to the critical curve), when
+// two images are closer than kMixedGapTrigger, when two rejected roots with residuals below
+// kSpuriousPair nearly coincide (kMixedRejGapTrigger, relative to sqrt(1 + |z|^2): a pair just
+// born at a fold, left as a near-double root), or when the FP32 image selection was flagged
+// (fallback, cap, ambiguous).
+constexpr float kMixedDetTrigger = 3e-2f;
+constexpr float kMixedGapTrigger = 1e-4f;
+constexpr float kMixedRejGapTrigger = 3e-2f;
+
+template <typename T>
+__device__ __forceinline__ uint8_t mixed_trigger_flags(const EpochOut<T>& o) {
+    return (uint8_t)(o.flag | (fmin(o.min_det, o.min_det_rej) < T(kMixedDetTrigger) ? FLAG_NEAR_DET : 0) |
+                     ((o.min_gap < T(kMixedGapTrigger) || o.min_gap_rej < T(kMixedRejGapTrigger)) ? FLAG_NEAR_GAP
+                                                                                                    : 0));
 }
 
 }  // namespace sblm

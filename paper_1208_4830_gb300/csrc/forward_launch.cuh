@@ -17,13 +17,6 @@ struct Bounds {
     double hi[SBLM_NPAR];
 };
 
-// MIXED: an epoch is re-solved in FP64 when an image, or a rejected root that nearly solves the
-// lens equation, has |det J| below this (next to a caustic FP32 loses accuracy, and an image pair
-// it failed to converge sits next to the critical curve), when two images are closer than the
-// gap trigger, or when the FP32 image selection was ambiguous
-constexpr float kMixedDetTrigger = 3e-2f;
-constexpr float kMixedGapTrigger = 1e-4f;
-
 // largest lightcurve staged in shared memory per block (larger ones are read from global memory)
 constexpr size_t kMaxStagedBytes = 96 * 1024;
 
@@ -41,16 +34,21 @@ struct ForwardArgs {
     double* chi2_out = nullptr;    // optional [n_cand]; null -> no chi^2
     int mode = SBLM_FP64;
     int G = 32;                    // threads per candidate (power of two, <= 256)
-    // MIXED only: queue of epochs to re-solve in FP64 (capacity entries of
-    // deferred_entry_bytes() each) and its counter; launch_forward zeroes the counter
-    void* queue = nullptr;
-    unsigned* queue_count = nullptr;
-    unsigned queue_cap = 0;
+    // MIXED only: mixed_scratch_bytes(n_cand, n_ep, chi2_out != null) bytes of device scratch
+    // (256-byte aligned) for the re-solve queue, its counter and the chi^2 terms; launch_forward
+    // zeroes the counter
+    void* mixed = nullptr;
 };
 
-// scratch of the MIXED re-solve queue: entry count sized for a few percent of the epochs (an
-// epoch that finds the queue full is re-solved in place, so the size is a speed choice only)
-unsigned mixed_queue_capacity(int n_cand, int n_ep);
+// MIXED scratch of one forward pass: the re-solve queue (an entry for one epoch in 32; an epoch
+// that finds it full is re-solved in place), its counter and, when chi^2 is wanted, the dense
+// n_cand x n_ep array of chi^2 terms that is summed row by row in a fixed order
+struct MixedLayout {
+    unsigned queue_cap = 0;
+    size_t off_count = 0, off_term = 0, bytes = 0;
+};
+MixedLayout mixed_layout(int n_cand, int n_ep, bool chi2);
+inline size_t mixed_scratch_bytes(int n_cand, int n_ep, bool chi2) { return mixed_layout(n_cand, n_ep, chi2).bytes; }
 size_t deferred_entry_bytes();
 
 size_t staged_bytes(int mode, bool chi2, int n_ep);

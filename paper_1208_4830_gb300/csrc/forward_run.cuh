@@ -93,22 +93,13 @@ __device__ __forceinline__ Cand group_candidate(const double* __restrict__ src, 
     return k;
 }
 
-// s + x as an unevaluated pair (hi, lo) of floats: Knuth's two-sum, then renormalisation
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
-    const float s = hi + x;
-    const float v = s - hi;
-    const float e = (hi - (s - v)) + (x - v);
-    const float t = lo + e;
-    hi = s + t;
-    lo = t - (hi - s);
-}
-
 // the MIXED re-solve's Aberth stop rule (relative correction), see solve_epoch
 constexpr double kResolveCubic = 1e-6;
 
 // FP64 re-solve of one deferred epoch (MIXED), warm-started from its FP32 roots; returns the
-// chi^2 term. Out of line: an FP32 lane that must do it in place keeps its state on the stack
-// instead of competing with the FP64 solver for registers.
+// chi^2 term from the FP64 flux fe and weight we = 1/sigma. Out of line: an FP32 lane that must
+// do it in place keeps its state on the stack instead of competing with the FP64 solver for
+// registers.
 static __device__ __noinline__ double resolve_fp64(const cx<float>* z32, uint32_t why, const Cand* kk,
                                                    double te, double fe, double we, double* A_row,
                                                    uint8_t* f_row, int e, bool chi2) {
@@ -124,14 +115,28 @@ static __device__ __noinline__ double resolve_fp64(const cx<float>* z32, uint32_
     return r * r;
 }
 
+// Where MIXED work goes. Epochs to re-solve in FP64 are appended to `queue` (slots taken with one
+// atomic per warp, so that a later pass re-solves them in full warps; an epoch that finds the queue
+// full is re-solved in place, so the capacity is a speed choice only). Every epoch's chi^2 term is
+// stored in the candidate's row of the dense term array (the FP32 ones here, the FP64 ones by the
+// re-solve, wherever it runs), and the row is summed afterwards in a fixed order: a MIXED chi^2
+// does not depend on the order in which the queue filled. `term_row` is the candidate's row
+// (epoch e at term_row[e]); null when no chi^2 is wanted.
+struct DeferSink {
+    Deferred* queue;
+    unsigned* queue_count;
+    unsigned queue_cap;
+};
+
 // The thread's epochs [e0, e1) of candidate k (all lanes of a warp run `seg` iterations so that
-// MIXED can reserve queue slots warp-wide). Writes A and flags when the row pointers are given;
-// returns the thread's chi^2 over the epochs it solved (MIXED: the queued epochs are left to the
-// re-solve pass; `c_tag` is the candidate index recorded in their queue entries).
+// MIXED can reserve queue slots warp-wide). Writes A and flags when the row pointers are given.
+// FP64 and FP32: returns the thread's chi^2 over its epochs, accumulated in FP64 in epoch order.
+// MIXED: writes each epoch's chi^2 term to term_row (CHI2) and returns 0; `c_tag` is the candidate
+// index recorded in its queue entries.
 template <int MODE, bool CHI2, bool STAGED>
 __device__ __forceinline__ double eval_run(const Cand& k, bool valid, int c_tag, int e0, int e1, int seg,
-                                           const LCView& lc, double* A_row, uint8_t* f_row, Deferred* queue,
-                                           unsigned* queue_count, unsigned queue_cap) {
+                                           const LCView& lc, double* A_row, uint8_t* f_row, const DeferSink& sink,
+                                           double* term_row) {
     double chi = 0.0;
     if constexpr (MODE == SBLM_FP64) {
         cx<double> z[5];
@@ -153,9 +158,6 @@ __device__ __forceinline__ double eval_run(const Cand& k, bool valid, int c_tag,
         const float itE = (float)k.inv_tE, sa = (float)k.sa, ca = (float)k.ca, u0 = (float)k.u0;
         const float d = (float)k.d, q = (float)k.q;
         const unsigned lane = threadIdx.x & 31u;
-        // per-thread chi^2 of the FP32 epochs as an unevaluated float pair (hi + lo): FP64-grade
-        // accumulation on the FP32 pipes; converted to FP64 for the cross-thread reduction
-        float chi_hi = 0.f, chi_lo = 0.f;
         cx<float> z[5];
         bool warm = false;
         for (int it = 0; it < seg; ++it) {
@@ -176,15 +178,17 @@ __device__ __forceinline__ double eval_run(const Cand& k, bool valid, int c_tag,
                 const float tau = diff_ff(ep.x, ep.y, t0h, t0l) * itE;
                 const cx<float> zeta = mk<float>(tau * sa + u0 * ca, -tau * ca + u0 * sa);
                 EpochOut<float> o = solve_epoch<float>(zeta, d, q, z, warm);
-                o.flag |= (fminf(o.min_det, o.min_det_rej) < kMixedDetTrigger ? FLAG_NEAR_DET : 0) |
-                          (o.min_gap < kMixedGapTrigger ? FLAG_NEAR_GAP : 0);
+                o.flag = mixed_trigger_flags(o);
                 if (MODE == SBLM_MIXED) defer = o.flag != 0;
                 why = o.flag;
                 if (A_row) A_row[e] = o.A;
                 if (f_row) f_row[e] = o.flag;
                 if (CHI2 && !defer) {
-                    const float r = (ep.z - o.A) * ep.w;
-                    ff_add(chi_hi, chi_lo, r * r);
+                    const double r = (double)((ep.z - o.A) * ep.w);
+                    if (MODE == SBLM_MIXED)
+                        term_row[e] = r * r;
+                    else
+                        chi += r * r;
                 }
             }
             if constexpr (MODE == SBLM_MIXED) {
@@ -193,40 +197,39 @@ __device__ __forceinline__ double eval_run(const Cand& k, bool valid, int c_tag,
                 if (b) {
                     const int leader = __ffs(b) - 1;
                     unsigned base = 0;
-                    if ((int)lane == leader) base = atomicAdd(queue_count, (unsigned)__popc(b));
+                    if ((int)lane == leader) base = atomicAdd(sink.queue_count, (unsigned)__popc(b));
                     base = __shfl_sync(0xffffffffu, base, leader);
                     if (defer) {
-                        const unsigned slot = base + __popc(b & ((1u << lane) - 1u));
-                        if (slot < queue_cap) {
-                            Deferred& qd = queue[slot];
+                        const unsigned slot = base + (unsigned)__popc(b & ((1u << lane) - 1u));
+                        if (slot < sink.queue_cap) {
+                            Deferred& qd = sink.queue[slot];
 #pragma unroll
                             for (int i = 0; i < 5; ++i) qd.z[i] = z[i];
                             qd.c = c_tag;
                             qd.e = e;
                             qd.why = why;
-                        } else {  // queue full: re-solve here
-                            double te, fe = 0.0, we = 0.0;
-                            if (STAGED) {
-                                const float4 ep = lc.s_ep[e];
-                                te = (double)ep.x + (double)ep.y;
-                                fe = ep.z;
-                                we = ep.w;
-                            } else {
-                                te = lc.t[e];
-                                if (CHI2) {
-                                    fe = lc.flux[e];
-                                    we = 1.0 / lc.sigma[e];
-                                }
-                            }
-                            chi += resolve_fp64(z, why, &k, te, fe, we, A_row, f_row, e, CHI2);
+                        } else {  // queue full: re-solve here, from the FP64 data
+                            const double te = lc.t[e];
+                            const double fe = CHI2 ? lc.flux[e] : 0.0, we = CHI2 ? 1.0 / lc.sigma[e] : 0.0;
+                            const double tm = resolve_fp64(z, why, &k, te, fe, we, A_row, f_row, e, CHI2);
+                            if (CHI2) term_row[e] = tm;
                         }
                     }
                 }
             }
         }
-        chi += (double)chi_hi + (double)chi_lo;
     }
     return chi;
+}
+
+// MIXED: sum of a candidate's term row over the lanes of its group of G threads (G a power of two
+// <= 32, groups aligned within the warp): lane g adds epochs g, g + G, ... in order, then a fixed
+// butterfly combines the lanes; every lane of the group gets the sum. All lanes of the warp call it.
+__device__ __forceinline__ double term_row_sum(const double* __restrict__ row, int n_ep, int g, int G, bool valid) {
+    double s = 0.0;
+    for (int e = g; valid && e < n_ep; e += G) s += row[e];
+    for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
 }
 
 }  // namespace sblm

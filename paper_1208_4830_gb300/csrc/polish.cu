@@ -19,7 +19,15 @@ __global__ void __launch_bounds__(kPolishThreads) polish_kernel(PolishArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[33];
     __shared__ unsigned s_qcount;
-    Deferred* queue = a.queue + (size_t)blockIdx.x * a.qcap;
+    DeferSink sink{};
+    double* term_row = nullptr;
+    if (MODE == SBLM_MIXED) {
+        char* m = static_cast<char*>(a.mixed) + (size_t)blockIdx.x * a.mx.block_bytes;
+        sink.queue = reinterpret_cast<Deferred*>(m);
+        sink.queue_count = &s_qcount;
+        sink.queue_cap = a.mx.queue_cap;
+        term_row = reinterpret_cast<double*>(m + a.mx.off_term);
+    }
     for (int lc = blockIdx.x; lc < a.n_lc; lc += gridDim.x) {
         const int64_t e0 = a.offsets ? a.offsets[lc] : 0;
         const int n_ep = a.offsets ? (int)(a.offsets[lc + 1] - e0) : a.n_ep;
@@ -28,7 +36,7 @@ __global__ void __launch_bounds__(kPolishThreads) polish_kernel(PolishArgs a) {
         for (int j = 0; j < kPolishN; ++j) g[j] = a.g_in[(size_t)lc * a.g_stride + j];
         double f = a.c_in ? a.c_in[(size_t)lc * a.c_stride] : INFINITY;
         double* A_row = a.blend ? a.A_scr + (size_t)blockIdx.x * a.A_stride : nullptr;
-        block_nelder_mead<MODE>(g, &f, a.maxfev, a.b, view, n_ep, queue, a.qcap, &s_qcount, s_red, A_row, a.f_min);
+        block_nelder_mead<MODE>(g, &f, a.maxfev, a.b, view, n_ep, sink, term_row, s_red, A_row, a.f_min);
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int j = 0; j < kPolishN; ++j) a.g_out[(size_t)lc * a.g_stride + j] = g[j];
@@ -38,19 +46,10 @@ __global__ void __launch_bounds__(kPolishThreads) polish_kernel(PolishArgs a) {
     }
 }
 
-int g_granted[3][64];
-
 template <int MODE>
 cudaError_t launch_mode(const PolishArgs& a, int blocks, size_t smem, cudaStream_t s) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = raise_smem_limit((const void*)polish_kernel<MODE>, smem);
     if (e != cudaSuccess) return e;
-    int& granted = g_granted[MODE][dev & 63];
-    if ((int)smem > granted) {
-        e = cudaFuncSetAttribute(polish_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        granted = (int)smem;
-    }
     polish_kernel<MODE><<<blocks, kPolishThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -61,22 +60,22 @@ size_t polish_smem_bytes(int mode, int max_ep) {
     return (size_t)max_ep * (mode == SBLM_FP64 ? 3 * sizeof(double) : sizeof(float4));
 }
 
-unsigned polish_queue_capacity(int mode, int max_ep) { return mode == SBLM_MIXED ? (unsigned)max_ep : 0; }
+PolishMixed polish_mixed_layout(int max_ep) {
+    PolishMixed l;
+    l.queue_cap = (unsigned)std::max(max_ep, 1);
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    l.off_term = up(sizeof(Deferred) * (size_t)l.queue_cap);
+    l.block_bytes = up(l.off_term + sizeof(double) * (size_t)l.queue_cap);
+    return l;
+}
 
 cudaError_t polish_prepare(int mode, int max_ep) {
     const size_t smem = polish_smem_bytes(mode, max_ep);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    int& granted = g_granted[mode][dev & 63];
-    if ((int)smem <= granted) return cudaSuccess;
     switch (mode) {
-        case SBLM_FP64: e = cudaFuncSetAttribute(polish_kernel<SBLM_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-        case SBLM_MIXED: e = cudaFuncSetAttribute(polish_kernel<SBLM_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-        default: e = cudaFuncSetAttribute(polish_kernel<SBLM_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+        case SBLM_FP64: return raise_smem_limit((const void*)polish_kernel<SBLM_FP64>, smem);
+        case SBLM_MIXED: return raise_smem_limit((const void*)polish_kernel<SBLM_MIXED>, smem);
+        default: return raise_smem_limit((const void*)polish_kernel<SBLM_FP32>, smem);
     }
-    if (e == cudaSuccess) granted = (int)smem;
-    return e;
 }
 
 cudaError_t launch_polish(int mode, const PolishArgs& a, int blocks, int max_ep, cudaStream_t s) {
@@ -139,8 +138,8 @@ extern "C" sblm_status sblm_polish_batch(const double* t, const double* flux, co
     SBLM_TRY(st.arg(genes_in, sizeof(double) * 6 * (size_t)n_lc, true, false, &i_gi));
     SBLM_TRY(st.arg(genes_out, sizeof(double) * 6 * (size_t)n_lc, false, true, &i_go));
     SBLM_TRY(st.arg(chi2_out, sizeof(double) * (size_t)n_lc, false, true, &i_c));
-    const unsigned qcap = polish_queue_capacity(precision, max_ep);
-    const int k_q = st.scratch(deferred_entry_bytes() * (size_t)qcap * blocks);
+    const PolishMixed mx = polish_mixed_layout(max_ep);
+    const int k_q = st.scratch(precision == SBLM_MIXED ? mx.block_bytes * (size_t)blocks : 0);
     const int k_A = st.scratch(blend ? sizeof(double) * (size_t)blocks * max_ep : 0);
     bool d1, d2, d3;
     SBLM_TRY(is_device_pointer(t, &d1));
@@ -162,8 +161,8 @@ extern "C" sblm_status sblm_polish_batch(const double* t, const double* flux, co
     a.g_out = static_cast<double*>(st.dev(i_go));
     a.c_out = static_cast<double*>(st.dev(i_c));
     a.maxfev = maxfev;
-    a.queue = static_cast<Deferred*>(st.scratch_ptr(k_q));
-    a.qcap = qcap;
+    a.mixed = st.scratch_ptr(k_q);
+    a.mx = mx;
     a.blend = blend ? 1 : 0;
     a.f_min = SBLM_BLEND_F_MIN;
     a.A_scr = blend ? static_cast<double*>(st.scratch_ptr(k_A)) : nullptr;

@@ -54,26 +54,31 @@ __device__ __forceinline__ void polish_fw(const LCView& v, int e, double& F, dou
 }
 
 // chi^2 of the candidate encoded by genes g (identical in every thread), all threads of the block;
-// with A_row (n_ep doubles of scratch) the chi^2 of the blended model with f profiled out
+// with A_row (n_ep doubles of scratch) the chi^2 of the blended model with f profiled out.
+// MIXED: every epoch's term goes to term_row (n_ep doubles of scratch), the queued epochs are
+// re-solved by the whole block from the FP64 data, and the row is summed in a fixed order, so the
+// value does not depend on scheduling.
 template <int MODE>
-__device__ double block_chi2(const double* g, const Bounds& b, const LCView& view, int n_ep, Deferred* queue,
-                             unsigned qcap, unsigned* s_qcount, double* s_red, double* A_row, double f_min) {
+__device__ double block_chi2(const double* g, const Bounds& b, const LCView& view, int n_ep, const DeferSink& sink,
+                             double* term_row, double* s_red, double* A_row, double f_min) {
     const Cand k = candidate<true>(g, b, 0);
     const int seg = (n_ep + blockDim.x - 1) / blockDim.x;
     const int e0 = min(n_ep, (int)threadIdx.x * seg), e1 = min(n_ep, e0 + seg);
     if (MODE == SBLM_MIXED) {
-        if (threadIdx.x == 0) *s_qcount = 0;
+        if (threadIdx.x == 0) *sink.queue_count = 0;
         __syncthreads();
     }
-    double chi = eval_run<MODE, true, true>(k, true, 0, e0, e1, seg, view, A_row, nullptr, queue, s_qcount, qcap);
+    double chi = eval_run<MODE, true, true>(k, true, 0, e0, e1, seg, view, A_row, nullptr, sink, term_row);
     if constexpr (MODE == SBLM_MIXED) {
         __syncthreads();
-        const unsigned n = min(*s_qcount, qcap);
+        const unsigned n = min(*sink.queue_count, sink.queue_cap);
         for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-            const Deferred q = queue[i];
-            const float4 ep = view.s_ep[q.e];
-            chi += resolve_fp64(q.z, q.why, &k, (double)ep.x + (double)ep.y, ep.z, ep.w, A_row, nullptr, q.e, true);
+            const Deferred q = sink.queue[i];
+            term_row[q.e] = resolve_fp64(q.z, q.why, &k, view.t[q.e], view.flux[q.e], 1.0 / view.sigma[q.e], A_row,
+                                         nullptr, q.e, true);
         }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n_ep; e += blockDim.x) chi += term_row[e];
     }
     if (A_row) {  // Section 4.4: f A + (1 - f) with f profiled out
         __syncthreads();
@@ -107,14 +112,14 @@ __device__ __forceinline__ double clamp01(double v) { return fmin(1.0, fmax(0.0,
 // hold the best vertex found (never worse than the start).
 template <int MODE>
 __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfev, const Bounds& b, const LCView& view,
-                                               int n_ep, Deferred* queue, unsigned qcap, unsigned* s_qcount,
-                                               double* s_red, double* A_row, double f_min) {
+                                               int n_ep, const DeferSink& sink, double* term_row, double* s_red,
+                                               double* A_row, double f_min) {
     constexpr int n = kPolishN;
     double x[n + 1][n], f[n + 1];
     double xb[n], xr[n], xt[n];
     for (int j = 0; j < n; ++j) x[0][j] = x0[j];
     f[0] = *f0;
-    if (!isfinite(f[0])) f[0] = block_chi2<MODE>(x[0], b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
+    if (!isfinite(f[0])) f[0] = block_chi2<MODE>(x[0], b, view, n_ep, sink, term_row, s_red, A_row, f_min);
     int fev = 0;
     bool build = true;
     while (fev < maxfev) {
@@ -122,7 +127,7 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
             for (int k = 0; k < n; ++k) {
                 for (int j = 0; j < n; ++j) x[k + 1][j] = x[0][j];
                 x[k + 1][k] = x[0][k] + (x[0][k] + kPolishDelta <= 1.0 ? kPolishDelta : -kPolishDelta);
-                f[k + 1] = block_chi2<MODE>(x[k + 1], b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
+                f[k + 1] = block_chi2<MODE>(x[k + 1], b, view, n_ep, sink, term_row, s_red, A_row, f_min);
             }
             fev += n;
             build = false;
@@ -153,12 +158,12 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
             xb[j] = __ddiv_rn(s, (double)n);
         }
         for (int j = 0; j < n; ++j) xr[j] = clamp01(__dsub_rn(__dmul_rn(2.0, xb[j]), x[n][j]));
-        const double fr = block_chi2<MODE>(xr, b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
+        const double fr = block_chi2<MODE>(xr, b, view, n_ep, sink, term_row, s_red, A_row, f_min);
         ++fev;
         bool shrink = false;
         if (fr < f[0]) {  // expansion
             for (int j = 0; j < n; ++j) xt[j] = clamp01(__dsub_rn(__dmul_rn(3.0, xb[j]), __dmul_rn(2.0, x[n][j])));
-            const double fe = block_chi2<MODE>(xt, b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
+            const double fe = block_chi2<MODE>(xt, b, view, n_ep, sink, term_row, s_red, A_row, f_min);
             ++fev;
             const bool take_e = fe < fr;
             for (int j = 0; j < n; ++j) x[n][j] = take_e ? xt[j] : xr[j];
@@ -172,7 +177,7 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
                 const double to = outside ? xr[j] : x[n][j];
                 xt[j] = clamp01(__dadd_rn(xb[j], __dmul_rn(0.5, __dsub_rn(to, xb[j]))));
             }
-            const double fc = block_chi2<MODE>(xt, b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
+            const double fc = block_chi2<MODE>(xt, b, view, n_ep, sink, term_row, s_red, A_row, f_min);
             ++fev;
             if (outside ? fc <= fr : fc < f[n]) {
                 for (int j = 0; j < n; ++j) x[n][j] = xt[j];
@@ -184,7 +189,7 @@ __device__ __noinline__ void block_nelder_mead(double* x0, double* f0, int maxfe
         if (shrink) {
             for (int k = 1; k <= n; ++k) {
                 for (int j = 0; j < n; ++j) x[k][j] = __dadd_rn(x[0][j], __dmul_rn(0.5, __dsub_rn(x[k][j], x[0][j])));
-                f[k] = block_chi2<MODE>(x[k], b, view, n_ep, queue, qcap, s_qcount, s_red, A_row, f_min);
+                f[k] = block_chi2<MODE>(x[k], b, view, n_ep, sink, term_row, s_red, A_row, f_min);
             }
             fev += n;
         }

@@ -15,6 +15,14 @@ constexpr int kPolishThreads = 256;
 constexpr int kPolishMaxFev = 1 << 20;
 constexpr size_t kPolishSmemBudget = 200 * 1024;
 
+// MIXED scratch of one polish block: a re-solve queue with room for every epoch of the longest
+// lightcurve and its chi^2 term row (forward_run.cuh: DeferSink)
+struct PolishMixed {
+    unsigned queue_cap = 0;
+    size_t off_term = 0, block_bytes = 0;
+};
+PolishMixed polish_mixed_layout(int max_ep);
+
 struct PolishArgs {
     const double* t;
     const double* flux;
@@ -30,8 +38,8 @@ struct PolishArgs {
     double* g_out;       // may alias g_in
     double* c_out;       // may alias c_in
     int maxfev;
-    Deferred* queue;     // MIXED: qcap entries per block
-    unsigned qcap;
+    void* mixed;         // MIXED: mx.block_bytes of scratch per block
+    PolishMixed mx;      // MIXED: polish_mixed_layout(longest lightcurve)
     int blend;           // chi^2 of the blended model with f profiled out (Section 4.4)
     double f_min;
     double* A_scr;       // blend: per block A_stride magnifications
@@ -39,7 +47,6 @@ struct PolishArgs {
 };
 
 size_t polish_smem_bytes(int mode, int max_ep);
-unsigned polish_queue_capacity(int mode, int max_ep);
 cudaError_t launch_polish(int mode, const PolishArgs& a, int blocks, int max_ep, cudaStream_t s);
 // set the kernel's shared-memory opt-in for `max_ep` (call before a stream capture)
 cudaError_t polish_prepare(int mode, int max_ep);

@@ -1,5 +1,6 @@
 // proposal.cuh -- one seed row of the EA drawn from the proposal network's Gaussian outputs, shared
-// by the sampling kernel and the batched fitter (which redraws its seeded rows at every restart).
+// by the sampling kernel and the batched fitter (which draws its seeded rows for the first
+// population only; restarts are the paper's random initialisation).
 #pragma once
 
 #include "common.cuh"

@@ -1,4 +1,5 @@
 // runtime.cu -- status strings, error reporting, pointer location, workspace, staging.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -42,6 +43,37 @@ sblm_status cuda_fail(cudaError_t e, const char* what) {
 
 CallLock::CallLock() { g_lock.lock(); }
 CallLock::~CallLock() { g_lock.unlock(); }
+
+namespace {
+std::mutex g_smem_lock;
+std::map<std::pair<const void*, int>, size_t> g_smem_granted;
+}  // namespace
+
+int device_sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    int sms = dev < 64 ? cached[dev].load() : 0;
+    if (sms > 0) return sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev < 64) cached[dev].store(sms);
+    return sms;
+}
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(g_smem_lock);
+    size_t& granted = g_smem_granted[{func, dev}];
+    if (bytes <= granted) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) granted = bytes;
+    return e;
+}
 
 sblm_status is_device_pointer(const void* p, bool* on_device) {
     cudaPointerAttributes a;

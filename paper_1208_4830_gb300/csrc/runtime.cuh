@@ -90,6 +90,14 @@ class Staging {
 sblm_status run_cached_graph(const std::vector<unsigned char>& key,
                              const std::function<cudaError_t(cudaStream_t)>& enqueue, cudaStream_t s);
 
+// Raise, never lower, the dynamic shared-memory limit of kernel `func` on the current device to
+// at least `bytes` (thread-safe; remembered per kernel and device). Call it before a launch, and
+// before any stream capture that contains the launch.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
+// Streaming multiprocessors of the current device (queried once per device; 1 if unknown).
+int device_sm_count();
+
 // Serialises calls that use a workspace (the lock is per process; calls are short to enqueue).
 struct CallLock {
     CallLock();

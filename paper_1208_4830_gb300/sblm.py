@@ -80,6 +80,11 @@ class BatchMonitor(ctypes.Structure):
     ]
 
 
+class BatchArchive(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_int32), ("top", ctypes.c_int32), ("radius", ctypes.c_double),
+                ("theta", ctypes.c_void_p), ("chi2", ctypes.c_void_p), ("count", ctypes.c_void_p)]
+
+
 class CnnTrainParams(ctypes.Structure):
     _fields_ = [
         ("batch", ctypes.c_int32),
@@ -140,6 +145,11 @@ _SIGS = {
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning), _p,
          ctypes.c_double, ctypes.POINTER(BatchMonitor), _p, _p, _p],
     ),
+    "sblm_fit_batch_archived": (
+        ctypes.c_int,
+        [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), ctypes.POINTER(BatchTuning),
+         ctypes.POINTER(BatchArchive), _p, _p, _p],
+    ),
     "sblm_polish_batch": (
         ctypes.c_int,
         [_p, _p, _p, _p, _i32, ctypes.POINTER(Bounds), _p, _i32, _i32, _p, _p, _p],
@@ -154,6 +164,7 @@ _SIGS = {
     "sblm_cnn_adamw": (ctypes.c_int, [_p, _p, _p, ctypes.POINTER(CnnTrainParams), ctypes.c_int64, _p]),
     "sblm_cnn_train": (ctypes.c_int, [_p, _p, ctypes.POINTER(CnnTrainParams), ctypes.c_int64, _i32, _p, _p]),
     "sblm_cnn_propose": (ctypes.c_int, [_p, _p, _i32, ctypes.POINTER(Bounds), _i32, _u64, _p, _p]),
+    "sblm_cnn_selftest_timeout": (ctypes.c_int, [_i32, _p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -465,6 +476,28 @@ def autotune_batch(t, flux, sigma, offsets, lo, hi, p, trial_generations=2, stre
     return best
 
 
+def fit_batch_archived(t, flux, sigma, offsets, lo, hi, p, size=8, radius=0.05, top=0, tuning=None, stream=None):
+    """fit_batch plus the solution archive (include/sblm.h: sblm_batch_archive): (best theta, chi^2,
+    archive theta [n_lc, size, 6], archive chi^2 [n_lc, size], solutions kept [n_lc]); unused
+    archive entries are NaN."""
+    n_lc = int(offsets.shape[0]) - 1
+    b = bounds(lo, hi)
+    best = np.empty((n_lc, 6))
+    best_chi2 = np.empty(n_lc)
+    a_th = np.empty((n_lc, size, 6))
+    a_c = np.empty((n_lc, size))
+    a_n = np.empty(n_lc, dtype=np.int32)
+    arc = BatchArchive(int(size), int(top), float(radius), a_th.ctypes.data, a_c.ctypes.data, a_n.ctypes.data)
+    tuning = _tuning(tuning, t, flux, sigma, offsets, lo, hi, p, stream)
+    a = [_ptr(x) for x in (t, flux, sigma, offsets)]
+    s = _stream(stream, t, flux, sigma)
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    st = _lib.sblm_fit_batch_archived(a[0][0], a[1][0], a[2][0], a[3][0], n_lc, ctypes.byref(b), ctypes.byref(p), tp,
+                                      ctypes.byref(arc), best.ctypes.data, best_chi2.ctypes.data, s)
+    _check(st, "sblm_fit_batch_archived")
+    return best, best_chi2, a_th, a_c, a_n
+
+
 def polish_batch(t, flux, sigma, offsets, lo, hi, genes, maxfev, precision="mixed", stream=None):
     """Amoeba fine-tuning of start genes [n_lc, 6]: (polished genes, chi^2)."""
     n_lc = int(offsets.shape[0]) - 1
@@ -643,6 +676,12 @@ def cnn_propose(out, window, lo, hi, n_seed, seed, stream=None):
                                _stream(stream, out, window))
     _check(st, "sblm_cnn_propose")
     return g
+
+
+def cnn_selftest_timeout(polls=1000, stream=None):
+    """Status (an int) of the bounded-wait self-test: SBLM_ETIMEOUT (4) when the wait on a barrier
+    that nothing arrives on gave up and the flag came back through the entry points' check."""
+    return int(_lib.sblm_cnn_selftest_timeout(int(polls), stream))
 
 
 def peak_rates(stream=None):

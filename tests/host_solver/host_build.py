@@ -36,14 +36,6 @@ def _host(src: str) -> str:
     return src
 
 
-def triggers():
-    """kMixedDetTrigger and kMixedGapTrigger as the library defines them."""
-    text = open(os.path.join(CSRC, "forward_launch.cuh")).read()
-    det = re.search(r"kMixedDetTrigger\s*=\s*([0-9.eE+-]+)f", text).group(1)
-    gap = re.search(r"kMixedGapTrigger\s*=\s*([0-9.eE+-]+)f", text).group(1)
-    return float(det), float(gap)
-
-
 def build(workdir: str) -> str:
     """Compile the host loop in ``workdir``; returns the executable's path."""
     gxx = shutil.which("g++")
@@ -58,13 +50,37 @@ def build(workdir: str) -> str:
     )
     open(os.path.join(workdir, "common.cuh"), "w").write(common)
     open(os.path.join(workdir, "forward.cuh"), "w").write(_host(open(os.path.join(CSRC, "forward.cuh")).read()))
-    det, gap = triggers()
     exe = os.path.join(workdir, "host_loop")
-    flags = ["-O2", "-std=c++17", "-ffp-contract=fast", f"-DDET_TRIGGER={det!r}f", f"-DGAP_TRIGGER={gap!r}f"]
+    flags = ["-O2", "-std=c++17", "-ffp-contract=fast"]
     if platform.machine() in ("x86_64", "AMD64"):
         flags.append("-mfma")  # fused multiply-adds, as on the GPU (native on aarch64)
     subprocess.run([gxx, *flags, "-I", workdir, os.path.join(HERE, "host_loop.cpp"), "-o", exe], check=True)
     return exe
+
+
+def build_count(workdir: str) -> str:
+    """Compile the operation-counting loop (count_loop.cpp) in ``workdir`` (after build())."""
+    gxx = shutil.which("g++")
+    exe = os.path.join(workdir, "count_loop")
+    shutil.copy(os.path.join(HERE, "count_types.h"), os.path.join(workdir, "count_types.h"))
+    subprocess.run([gxx, "-O2", "-std=c++17", "-I", workdir, os.path.join(HERE, "count_loop.cpp"), "-o", exe],
+                   check=True)
+    return exe
+
+
+def count(exe: str, theta, t, flux, sigma, seg: int, workdir: str):
+    """(epochs, FP32 operations, FP64 operations, epochs re-solved in FP64) of the MIXED epoch
+    loop over every (row, epoch); runs of ``seg`` epochs start cold."""
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    n, m = theta.shape[0], np.asarray(t).size
+    src = os.path.join(workdir, "count_in.bin")
+    with open(src, "wb") as f:
+        np.array([n, m, seg], dtype=np.int32).tofile(f)
+        for a in (t, flux, 1.0 / np.asarray(sigma, dtype=np.float64)):
+            np.ascontiguousarray(a, dtype=np.float64).tofile(f)
+        theta.tofile(f)
+    out = subprocess.run([exe, src], check=True, capture_output=True, text=True).stdout.split()
+    return tuple(int(x) for x in out)
 
 
 def run(exe: str, theta, t, seg: int, workdir: str):

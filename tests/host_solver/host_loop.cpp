@@ -12,12 +12,6 @@
 
 #include "forward.cuh"
 
-#ifndef DET_TRIGGER
-#error "DET_TRIGGER (kMixedDetTrigger) must be defined"
-#endif
-#ifndef GAP_TRIGGER
-#error "GAP_TRIGGER (kMixedGapTrigger) must be defined"
-#endif
 
 using namespace sblm;
 
@@ -50,8 +44,7 @@ int main(int argc, char** argv) {
             const float tau = diff_ff(thi, tlo, t0h, t0l) * itE;
             const cx<float> zeta = mk<float>(tau * fsa + fu0 * fca, -tau * fca + fu0 * fsa);
             EpochOut<float> o = solve_epoch<float>(zeta, (float)d, (float)q, z, warm);
-            o.flag |= (fminf(o.min_det, o.min_det_rej) < DET_TRIGGER ? FLAG_NEAR_DET : 0) |
-                      (o.min_gap < GAP_TRIGGER ? FLAG_NEAR_GAP : 0);
+            o.flag = mixed_trigger_flags(o);
             A32[(size_t)r * n_ep + e] = o.A;
             fl[(size_t)r * n_ep + e] = o.flag;
             const double tau64 = (t[e] - t0) * inv_tE;

@@ -29,6 +29,99 @@ def _cos(a, b):
     return float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
+# element-wise check: BF16 unit roundoff, FP32 accumulation; errors taken as random (root of the
+# sum of squares of the independent rounding contributions) and checked at ELEM_SIGMAS of that scale
+U_BF16 = 2.0 ** -8
+U_F32 = 2.0 ** -24
+ELEM_SIGMAS = 8.0
+
+
+def _gelu_dd(z):
+    """Second derivative of x Phi(x): phi(x) (2 - x^2)."""
+    return np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi) * (2.0 - z * z)
+
+
+def _rss(a, b):
+    """sqrt(sum_k a_k^2 b_k^2) of every dot product of a @ b."""
+    return np.sqrt((a * a) @ (b * b))
+
+
+def _q(*terms):
+    return np.sqrt(sum(t * t for t in terms))
+
+
+def _elementwise_scales(w, x, y):
+    """Error scale of every network output and every gradient element when each product's
+    operands are rounded to BF16 (unit roundoff u = 2^-8, both operands), products accumulate in
+    FP32, activations and backward signals are stored in BF16, and the errors of earlier layers
+    propagate through the weights, GELU', GELU'' and the loss's derivatives. Rounding errors are
+    treated as independent, so a dot product sum_k a_k b_k gets
+    sqrt(sum_k (da_k b_k)^2 + (a_k db_k)^2) + sqrt(2) u sqrt(sum_k (a_k b_k)^2): the size of the
+    error a correct BF16 computation makes, element by element, while an element computed wrongly
+    is off by a sizeable part of its value. The scales follow the oracle's own passes."""
+    p = ocnn.unflatten(w)
+    u, r2 = U_BF16, math.sqrt(2.0)
+    out, (cache, f, z5, h5) = ocnn.forward(w, x)
+    h, e_h = np.asarray(x, float), U_BF16 * np.abs(x)
+    hs, ezs = [], []
+    for i, (_, _, stride) in enumerate(ocnn.CONVS):
+        W = p[f"W{i + 1}"]
+        cols, cols_e = ocnn.im2col(h, stride), ocnn.im2col(e_h, stride)
+        K = cols.shape[-1]
+        e_z = _q(_rss(cols_e, W), (r2 * u + K * U_F32) * _rss(cols, W))
+        z = cache[i][2]
+        hs.append((h, e_h))
+        ezs.append(e_z)
+        h = ocnn.gelu(z)
+        e_h = _q(ocnn.gelu_grad(z) * e_z, u * h)
+    B = h.shape[0]
+    fv, fe = h.reshape(B, -1), e_h.reshape(B, -1)
+    W5, W6 = p["W5"], p["W6"]
+    e_z5 = _q(_rss(fe, W5), (r2 * u + fv.shape[1] * U_F32) * _rss(fv, W5))
+    e_h5 = _q(ocnn.gelu_grad(z5) * e_z5, u * h5)
+    e_out = _q(_rss(e_h5, W6), (r2 * u + 128 * U_F32) * _rss(h5, W6))
+    # backward
+    _, dout = ocnn.nll(out, y)
+    mu, sv = out[:, :6], out[:, 6:]
+    r, ex = y - mu, np.exp(-sv)
+    e_mu, e_s = e_out[:, :6], e_out[:, 6:]
+    e_dout = np.empty_like(dout)
+    e_dout[:, :6] = _q(ex / B * e_mu, r * ex / B * e_s, u * dout[:, :6])
+    e_dout[:, 6:] = _q(r * ex / B * e_mu, 0.5 * r * r * ex / B * e_s, u * dout[:, 6:])
+    g = {}
+    g["W6"] = _q(_rss(e_h5.T, dout), _rss(h5.T, e_dout), (r2 * u + B * U_F32) * _rss(h5.T, dout))
+    g["b6"] = _q(np.sqrt((e_dout ** 2).sum(0)), B * U_F32 * np.sqrt((dout ** 2).sum(0)))
+    dh5 = dout @ W6.T
+    e_dh5 = _q(_rss(e_dout, W6.T), (r2 * u + 12 * U_F32) * _rss(dout, W6.T))
+    gd5 = ocnn.gelu_grad(z5)
+    dz5 = dh5 * gd5
+    e_dz5 = _q(e_dh5 * gd5, dh5 * _gelu_dd(z5) * e_z5, u * dz5)
+    g["W5"] = _q(_rss(fe.T, dz5), _rss(fv.T, e_dz5), (r2 * u + B * U_F32) * _rss(fv.T, dz5))
+    g["b5"] = _q(np.sqrt((e_dz5 ** 2).sum(0)), B * U_F32 * np.sqrt((dz5 ** 2).sum(0)))
+    dh = (dz5 @ W5.T).reshape(B, 32, ocnn.WIDTH)
+    e_dh = _q(_rss(e_dz5, W5.T), (r2 * u + 128 * U_F32) * _rss(dz5, W5.T)).reshape(B, 32, ocnn.WIDTH)
+    for i in reversed(range(len(ocnn.CONVS))):
+        shape, cols, z, stride = cache[i]
+        e_z = ezs[i]
+        hin, e_hin = hs[i]
+        gd = ocnn.gelu_grad(z)
+        dz = dh * gd
+        e_dz = _q(e_dh * gd, dh * _gelu_dd(z) * e_z, u * dz)
+        Bq, Lo, Co = dz.shape
+        cv = cols.reshape(Bq * Lo, -1)
+        ce = ocnn.im2col(e_hin, stride).reshape(Bq * Lo, -1)
+        dzv, edz = dz.reshape(Bq * Lo, Co), e_dz.reshape(Bq * Lo, Co)
+        g[f"W{i + 1}"] = _q(_rss(ce.T, dzv), _rss(cv.T, edz), (r2 * u + Bq * Lo * U_F32) * _rss(cv.T, dzv))
+        g[f"b{i + 1}"] = _q(np.sqrt((edz ** 2).sum(0)), Bq * Lo * U_F32 * np.sqrt((dzv ** 2).sum(0)))
+        if i > 0:
+            W = p[f"W{i + 1}"]
+            dcols = dz @ W.T
+            e_dcols = _q(_rss(e_dz, W.T), (r2 * u + Co * U_F32) * _rss(dz, W.T))
+            dh = ocnn.col2im(dcols, shape[1], shape[2], stride)
+            e_dh = np.sqrt(ocnn.col2im(e_dcols ** 2, shape[1], shape[2], stride))
+    return e_out, ocnn.flatten(g)
+
+
 def _weights(seed, bias_scale=0.1):
     """Oracle initial weights with non-zero biases, so every term of the gradient is exercised."""
     w = op.init_params(seed)
@@ -63,6 +156,9 @@ def test_forward_matches_oracle(lib, B):
                           torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
     ref, _ = ocnn.forward(w, x)
     assert _rel(out, ref) <= BF16_REL, _rel(out, ref)
+    e_out, _ = _elementwise_scales(w, x, np.zeros((B, 6)))
+    ratio = np.abs(out - ref) / (e_out + 1e-30)
+    assert ratio.max() <= ELEM_SIGMAS, ratio.max()
 
 
 @pytest.mark.parametrize("B", [3, 64, 130])
@@ -76,6 +172,10 @@ def test_gradients_match_oracle(lib, B):
     g = g.cpu().numpy().astype(np.float64)
     ref_loss, ref_g = ocnn.loss_and_grad(w, x, y)
     assert loss == pytest.approx(ref_loss, rel=BF16_REL)
+    # element by element: every gradient element within ELEM_SIGMAS of its own rounding scale
+    _, e_g = _elementwise_scales(w, x, y)
+    ratio = np.abs(g - ref_g) / (e_g + 1e-30)
+    assert ratio.max() <= ELEM_SIGMAS, (int(np.argmax(ratio)), ratio.max())
     o = 0
     for name, shape in ocnn.SHAPES:
         n = int(np.prod(shape))
@@ -266,3 +366,17 @@ def test_training_batch_size_properties(lib):
     gm = np.mean([p[1].cpu().numpy().astype(np.float64) for p in parts], axis=0)
     assert L == pytest.approx(Lm, rel=1e-6)
     assert _rel(g.cpu().numpy().astype(np.float64), gm) <= 1e-5
+
+
+def test_bounded_wait_gives_up_and_reports(lib):
+    """The tensor-core kernels bound every mbarrier wait. A block waiting on a barrier that nothing
+    arrives on must give up after its poll budget, set the device flag, and the entry points'
+    check must turn it into SBLM_ETIMEOUT and clear it: the next call on the device succeeds."""
+    assert lib.cnn_selftest_timeout(polls=1000) == 4  # SBLM_ETIMEOUT
+    assert lib.cnn_selftest_timeout(polls=1) == 4
+    w = _weights(1)
+    x, y = _inputs(3, 4)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    loss, _ = lib.cnn_loss_grad(torch.tensor(w, **f32), torch.tensor(x, **f32), torch.tensor(y, **f32))
+    assert np.isfinite(loss)
+

@@ -6,9 +6,11 @@ the magnification is not steep in the source plane: FP32 rounds the source posit
 |zeta|, which moves A by |grad_zeta ln A| max(1, |zeta|) times that ("steepness", computed from
 the oracle by central differences), so "away from caustics" for FP32 also asks the steepness to
 stay at most 30. Wherever |det J| >= 1e-3 the FP32 error must stay within
-1e-6 * max(1, steepness, 1/|det J|). MIXED re-solves
-the epochs next to caustics in FP64; there it must match to 1e-8. Points the oracle flags are
-excluded, and so are FP32 points that the device itself flags as undecidable in FP32.
+1e-6 * max(1, steepness, 1/|det J|). MIXED re-solves the epochs next to caustics in FP64; there it
+must match to 1e-8. Which points are checked is decided by the oracle alone (its own flag, its
+|det J| and the steepness). FP32 without re-solves cannot decide a few of them (an image pair it
+does not resolve drops out with opposite parities): every FP32 point outside its bound must carry
+one of the device's FP32 flags, and such points stay below 2% of the checked ones.
 """
 import numpy as np
 import pytest
@@ -21,8 +23,10 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "fp32": 1e-5, "mixed": 1e-5}
 DET_AWAY = {"fp64": 1e-3, "fp32": 1e-2, "mixed": 1e-2}
-FLAG_FALLBACK, FLAG_FP64, FLAG_CAP, FLAG_AMBIGUOUS = 1, 2, 4, 8
+FLAG_FALLBACK, FLAG_FP64, FLAG_CAP, FLAG_AMBIGUOUS, FLAG_NEAR_DET, FLAG_NEAR_GAP = 1, 2, 4, 8, 16, 32
+FP32_FLAGS = FLAG_FALLBACK | FLAG_CAP | FLAG_AMBIGUOUS | FLAG_NEAR_DET | FLAG_NEAR_GAP
 STEEP = 30.0
+FP32_UNDECIDED = 0.02
 
 
 def dev(x):
@@ -44,25 +48,31 @@ def sweep():
     return sw, A, info
 
 
+def _allow_flagged(bad, fl, checked, prec):
+    """The points of `checked` outside their bound (`bad`): none, except in FP32, where each must
+    carry a device flag and they stay below FP32_UNDECIDED of the checked points."""
+    if prec != "fp32":
+        return not bad.any()
+    return bool(np.all((fl[bad] & FP32_FLAGS) != 0)) and bad.sum() <= FP32_UNDECIDED * max(1, checked.sum())
+
+
 def check_parity(A, fl, A_ref, info, prec, min_share=0.9):
     """Assert the tolerances above; returns the share of points checked at the strict bound."""
     assert np.all(np.isfinite(A)) and np.all(A >= 1.0 - 1e-6)
     err = np.abs(A - A_ref) / A_ref
     md = info["min_det"]
     usable = ~info["flag"]
-    if prec != "mixed":
-        gpu_unsure = (fl & (FLAG_FALLBACK | FLAG_AMBIGUOUS)) != 0
-        assert gpu_unsure.mean() < 0.02, gpu_unsure.mean()
-        usable &= ~gpu_unsure
     strict = usable & (md >= DET_AWAY[prec])
     if prec != "fp64":
         strict &= info["steep"] <= STEEP
     assert strict.mean() >= min_share
-    assert err[strict].max() <= TOL[prec], (prec, err[strict].max())
+    bad = strict & (err > TOL[prec])
+    assert _allow_flagged(bad, fl, strict, prec), (prec, err[strict].max(), bad.sum(), strict.sum())
     if prec != "fp64":
         wide = usable & (md >= 1e-3)
         bound = 1e-6 * np.maximum(np.maximum(1.0, info["steep"]), 1.0 / md)
-        assert np.all(err[wide] <= bound[wide]), (prec, (err[wide] / bound[wide]).max())
+        bad = wide & (err > bound)
+        assert _allow_flagged(bad, fl, wide, prec), (prec, (err[wide] / bound[wide]).max(), bad.sum())
     if prec == "mixed":
         re = ((fl & FLAG_FP64) != 0) & usable & (md >= 1e-6)
         if re.any():
@@ -90,11 +100,15 @@ def test_chi2_parity(lib, sweep, prec):
     rows = ((info["min_det"] >= DET_AWAY[prec]) & ~info["flag"]).all(axis=1)
     if prec != "fp64":
         rows &= (info["steep"] <= STEEP).all(axis=1)
-    if prec == "fp32":
-        _, fl = lib.magnification(dev(sw.theta), dev(sw.t), prec, flags=True)
-        rows &= ((fl.cpu().numpy() & (FLAG_FALLBACK | FLAG_AMBIGUOUS)) == 0).all(axis=1)
     assert rows.sum() >= 10
-    np.testing.assert_allclose(c[rows], ref[rows], rtol=TOL[prec], atol=0)
+    bad = rows & (np.abs(c - ref) > TOL[prec] * ref)
+    if prec == "fp32":
+        # a row FP32 gets wrong must contain an epoch the device flagged as undecidable in FP32
+        _, fl = lib.magnification(dev(sw.theta), dev(sw.t), prec, flags=True)
+        flagged = ((fl.cpu().numpy() & (FLAG_FALLBACK | FLAG_AMBIGUOUS)) != 0).any(axis=1)
+        assert np.all(flagged[bad]) and bad.sum() <= 0.1 * rows.sum(), (bad.sum(), rows.sum())
+    else:
+        assert not bad.any(), (prec, np.max(np.abs(c - ref)[rows] / ref[rows]))
 
 
 def test_host_pointers_equal_device_pointers(lib, sweep):
@@ -199,5 +213,10 @@ def test_mixed_chi2_of_the_full_sweep_against_fp64(lib):
     assert np.median(err) < 1e-6
     assert err.max() <= 1e-2, (int(np.argmax(err)), err.max())
     assert np.mean(err > 1e-3) <= 0.005, np.mean(err > 1e-3)
-    # the trajectories not aimed at a caustic (most of the sweep) rarely meet one
-    assert np.mean(err[~sw.forced] > 1e-3) <= 0.002
+    # the trajectories not aimed at a caustic (most of the sweep) rarely meet one. The FP32 error of
+    # a magnification, ~1e-6 max(1, steepness) relative, moves a residual (F - A)/sigma by ~1e-4
+    # when sigma is 1% of the flux, so rows whose model runs close to the data reach relative
+    # chi^2 errors of 1e-4 from FP32 rounding alone: 1e-4 bounds most rows, 1e-3 nearly all
+    unforced = err[~sw.forced]
+    assert np.mean(unforced > 1e-4) <= 0.01, np.mean(unforced > 1e-4)
+    assert np.mean(unforced > 1e-3) <= 0.002, np.mean(unforced > 1e-3)

@@ -91,3 +91,63 @@ def test_fp64_loop_meets_the_device_parity_bound(loop):
     assert ok.mean() >= 0.9
     err = np.abs(A64 - A_ref) / A_ref
     assert err[ok].max() <= 1e-10, err[ok].max()
+
+
+def test_near_double_root_pairs_are_re_solved(loop):
+    """Candidates near held-out truths (500 epochs, 32 per device thread) where the FP32 iteration
+    left an image pair born at a fold as one near-double root: residuals of 3-8%, |det J| about
+    0.1 at the stuck roots, so neither the |det J| nor the image-gap trigger fired, and MIXED kept
+    magnifications off by 63-97% (7.9 for 21.4, 3.6 for 73.6). The near-double-root trigger
+    (two rejected roots with residuals below 0.25 closer than 3e-2 sqrt(1 + |z|^2)) must now re-solve
+    them, and every epoch MIXED keeps in FP32 stays within 1e-2 of the FP64 loop."""
+    wd, exe = loop
+    b = synth.heldout_batch(256, seed=77, n_ep=500)
+    cases = [
+        (70, 291, [3.7552689721065864, 27.858616385898436, 0.07166469658894722, 2.606638072653452,
+                   0.8421408336742223, 0.18747443275149916]),
+        (70, 294, [3.6537459065846396, 30.60189712140481, 0.06927339386021561, 2.604919068603876,
+                   0.9147765737218083, 0.17769610407273015]),
+        (11, 104, [-19.36383977832547, 80.65740278539056, 0.042208674430312926, 5.803938306196384,
+                   1.6560003012985136, 0.16239519005486136]),
+        (56, 485, [18.58063636891368, 77.63440801180013, 0.24180110605852936, 2.2465960058034797,
+                   1.4613757510404177, 0.5981700439422707]),
+    ]
+    for lc, e, th in cases:
+        t = b.t[b.offsets[lc] : b.offsets[lc + 1]]
+        A32, fl, A64 = host_build.run(exe, np.array([th]), t, 32, wd)
+        assert abs(A64[0, e] / A32[0, e] - 1) > 0.5 or fl[0, e] != 0  # FP32 alone is far off here
+        assert fl[0, e] != 0, (lc, e)
+        kept = fl[0] == 0
+        assert np.max(np.abs(A32[0, kept] / A64[0, kept] - 1)) <= 1e-2
+
+
+def test_operation_counts_match_hand_counts(loop):
+    """The counting types behind the roofline's algorithmic operation count, against hand counts of
+    two formulas: the quintic's coefficients (Eq. lensingPoly, general mass pair) take 123 real
+    operations (complex products 6, complex sums 2, real-by-complex products 2) and one Horner
+    pass with its derivative over degree 5 takes 5 x (2 complex products + 2 complex sums) = 80."""
+    wd, _ = loop
+    exe = host_build.build_count(wd)
+    import subprocess
+
+    out = subprocess.run([exe, "--pins"], check=True, capture_output=True, text=True).stdout.split()
+    assert [int(x) for x in out] == [123, 80]
+
+
+def test_operation_count_per_magnification(loop):
+    """Algorithmic FP32 operations per magnification of the MIXED epoch loop on sweep candidates:
+    a few thousand (one quintic, two to four Aberth sweeps of five root updates, the image
+    selection), fewer when runs are long (fewer cold starts), and FP64 work only for re-solved
+    epochs (a full FP64 solve each)."""
+    wd, _ = loop
+    exe = host_build.build_count(wd)
+    sw = synth.forward_sweep(n_cand=256, n_ep=1000, seed=4)
+    A = osb.magnification(sw.truth[None, :], sw.t)[0]
+    sigma = sw.sigma_frac * A
+    flux = A + sigma * sw.z
+    rows = np.arange(0, 256, 8)
+    n, f32_short, f64, deferred = host_build.count(exe, sw.theta[rows], sw.t, flux, sigma, 8, wd)
+    _, f32_long, _, _ = host_build.count(exe, sw.theta[rows], sw.t, flux, sigma, 250, wd)
+    assert n == rows.size * 1000
+    assert 1500 < f32_long / n < f32_short / n < 5000
+    assert deferred > 0 and 500 < f64 / deferred < 10000

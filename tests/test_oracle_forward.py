@@ -276,3 +276,23 @@ def test_blend_fit_clamps():
     assert f == S.BLEND_F_MIN
     c, f = S.blend_fit(np.ones(5), np.ones(5) * 1.1, sigma)  # flat model: f = 1 by convention
     assert f == 1.0 and c == pytest.approx(5 * 1.0)
+
+
+def test_steepness_closed_form_in_the_point_lens_limit():
+    """steepness = |grad_zeta ln A| max(1, |zeta|). For a single lens, A depends on u = |zeta| only
+    and d ln A / du = -8 / (u (u^2 + 2) (u^2 + 4)) (differentiating Paczynski's formula), so the
+    steepness of a binary with a small secondary (q = 1e-6, deviations O(q)) far from the source
+    is that closed form times max(1, u): it pins the central differences, the gradient's two directions, the
+    normalisation by A and the max(1, |zeta|) factor (u runs from 0.05 to 4)."""
+    t = np.linspace(-30.0, 30.0, 61)
+    rows = []
+    for u0, alpha in ((0.05, 0.3), (0.4, 2.0), (1.2, 4.0), (2.5, 5.5)):
+        rows.append([0.0, 10.0, u0, alpha, 2.9, 1e-6])
+    theta = np.array(rows)
+    steep = S.steepness(theta, t)
+    zeta = S.source_position(t[None, :], theta[:, 0:1], theta[:, 1:2], theta[:, 2:3], theta[:, 3:4])
+    u = np.abs(zeta)
+    far = np.abs(zeta - 2.9) > 0.05  # away from the secondary's (tiny) caustic
+    expect = 8.0 / (u * (u * u + 2.0) * (u * u + 4.0)) * np.maximum(1.0, u)
+    assert far.mean() > 0.9 and u.min() < 0.1 and u.max() > 3.0
+    np.testing.assert_allclose(steep[far], expect[far], rtol=1e-4)
