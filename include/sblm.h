@@ -199,6 +199,18 @@ sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t n_pop, int
                                int32_t generation, sblm_ea_state* state, void* stream);
 
 /*
+ * sblm_ea_generation for n_pops independent populations at once (no counterpart in the paper: a
+ * throughput form of Appendix A's generation for callers that evolve many populations, e.g. one
+ * per lightcurve, from the host). P [n_pops * n_pop * n_par], chi2 [n_pops * n_pop] and states
+ * [n_pops] hold the populations back to back; population b uses stream id stream_id0 + b and is
+ * ranked by its own block, all in one launch of each operator kernel. The results equal n_pops
+ * calls of sblm_ea_generation (population b with stream id stream_id0 + b). 1 <= n_pops <= 65535.
+ */
+sblm_status sblm_ea_generation_batch(double* P, const double* chi2, int32_t n_pops, int32_t n_pop,
+                                     int32_t n_par, const sblm_ea_params* params, uint64_t stream_id0,
+                                     int32_t generation, sblm_ea_state* states, void* stream);
+
+/*
  * sblm_ea_generation without any allocation. The paper has no counterpart: this is a library
  * convenience for callers that must not allocate device memory while they run, for example a
  * pipeline that reserves all of its GPU memory up front and may not grow it later, or a host

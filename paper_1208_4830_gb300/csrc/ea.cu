@@ -41,11 +41,23 @@ __global__ void state_reset_kernel(EAConst c, sblm_ea_state* state) {
     *state = s;
 }
 
+// block b ranks population b of a batch (its rows, chi^2, state, order, control word and keys
+// at b times the per-population strides; stream id c.stream + b); a single population is b = 0
 __global__ void __launch_bounds__(kRankThreads)
     rank_kernel(EAConst c, int gen, const double* __restrict__ chi2, const double* __restrict__ P,
                 sblm_ea_state* __restrict__ state, int* __restrict__ order, EACtrl* __restrict__ ctrl,
                 uint64_t* __restrict__ keys, double* __restrict__ trace_row, int produce) {
     extern __shared__ __align__(16) unsigned char smem[];
+    {
+        const size_t b = blockIdx.x, m = (size_t)c.n_pop * c.n_par;
+        chi2 += b * c.n_pop;
+        P += b * m;
+        state += b;
+        order += b * c.n_pop;
+        ctrl += b;
+        keys += b * m;
+        c.stream += b;
+    }
     int n2 = 1;
     while (n2 < c.n_pop) n2 <<= 1;
     double* skey = reinterpret_cast<double*>(smem);
@@ -76,10 +88,20 @@ __global__ void __launch_bounds__(kRankThreads)
     }
 }
 
+// grid row blockIdx.y is population y of a batch (strides as in rank_kernel)
 __global__ void offspring_kernel(EAConst c, int gen, const double* __restrict__ P, const int* __restrict__ order,
                                  const EACtrl* __restrict__ ctrl, const uint64_t* __restrict__ keys,
                                  double* __restrict__ P_next) {
-    if (ctrl->restart) {  // uniform over the grid
+    {
+        const size_t b = blockIdx.y, m = (size_t)c.n_pop * c.n_par;
+        P += b * m;
+        order += b * c.n_pop;
+        ctrl += b;
+        keys += b * m;
+        P_next += b * m;
+        c.stream += b;
+    }
+    if (ctrl->restart) {  // uniform over the grid row
         __shared__ uint64_t tile[kInitTile];
         const int m = c.n_pop * c.n_par;
         block_init_values(c, gen + 1, keys, m, P_next, blockIdx.x * blockDim.x, m, tile, kInitTile);
@@ -138,21 +160,23 @@ cudaError_t launch_state_reset(const EAConst& c, sblm_ea_state* state, cudaStrea
 }
 
 cudaError_t launch_rank(const EAConst& c, int gen, const double* chi2, const double* P, sblm_ea_state* state,
-                        int* order, EACtrl* ctrl, uint64_t* keys, double* trace_row, bool produce, cudaStream_t s) {
+                        int* order, EACtrl* ctrl, uint64_t* keys, double* trace_row, bool produce, cudaStream_t s,
+                        int n_pops) {
     int n2 = 1;
     while (n2 < c.n_pop) n2 <<= 1;
     const size_t smem = (size_t)n2 * (sizeof(double) + sizeof(int));
     // opt in beyond 48 KB (with the kernel's static shared memory)
     cudaError_t e = raise_smem_limit((const void*)rank_kernel, smem);
     if (e != cudaSuccess) return e;
-    rank_kernel<<<1, kRankThreads, smem, s>>>(c, gen, chi2, P, state, order, ctrl, keys, trace_row, produce ? 1 : 0);
+    rank_kernel<<<n_pops, kRankThreads, smem, s>>>(c, gen, chi2, P, state, order, ctrl, keys, trace_row,
+                                                   produce ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_offspring(const EAConst& c, int gen, const double* P, const int* order, const EACtrl* ctrl,
-                             const uint64_t* keys, double* P_next, cudaStream_t s) {
+                             const uint64_t* keys, double* P_next, cudaStream_t s, int n_pops) {
     const int m = c.n_pop * c.n_par;
-    offspring_kernel<<<blocks_for(m, 256), 256, 0, s>>>(c, gen, P, order, ctrl, keys, P_next);
+    offspring_kernel<<<dim3(blocks_for(m, 256), n_pops), 256, 0, s>>>(c, gen, P, order, ctrl, keys, P_next);
     return cudaGetLastError();
 }
 
@@ -208,6 +232,39 @@ extern "C" sblm_status sblm_ea_generation(double* P, const double* chi2, int32_t
                           static_cast<sblm_ea_state*>(st.dev(i_s)), order, ctrl, keys, nullptr, true, s));
     SBLM_CUDA(launch_offspring(c, generation, dP, order, ctrl, keys, dN, s));
     SBLM_CUDA(cudaMemcpyAsync(dP, dN, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    return st.end();
+}
+
+extern "C" sblm_status sblm_ea_generation_batch(double* P, const double* chi2, int32_t n_pops, int32_t n_pop,
+                                                int32_t n_par, const sblm_ea_params* params, uint64_t stream_id0,
+                                                int32_t generation, sblm_ea_state* states, void* stream) {
+    EAConst c;
+    SBLM_TRY(ea_const(params, n_pop, n_par, stream_id0, &c));
+    if (n_pops < 1 || n_pops > 65535) return fail(SBLM_EINVAL, "n_pops=%d outside [1, 65535]", n_pops);
+    if (!P || !chi2 || !states) return fail(SBLM_EINVAL, "P, chi2 and states are required");
+    if (generation < 0) return fail(SBLM_EINVAL, "generation must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallLock lock;
+    Staging st(s);
+    const size_t m = (size_t)n_pop * n_par, all = m * n_pops;
+    int i_P, i_c, i_s;
+    SBLM_TRY(st.arg(P, sizeof(double) * all, true, true, &i_P));
+    SBLM_TRY(st.arg(chi2, sizeof(double) * (size_t)n_pop * n_pops, true, false, &i_c));
+    SBLM_TRY(st.arg(states, sizeof(sblm_ea_state) * (size_t)n_pops, true, true, &i_s));
+    const int k_order = st.scratch(sizeof(int) * (size_t)n_pop * n_pops);
+    const int k_ctrl = st.scratch(sizeof(EACtrl) * (size_t)n_pops);
+    const int k_keys = st.scratch(sizeof(uint64_t) * all);
+    const int k_next = st.scratch(sizeof(double) * all);
+    SBLM_TRY(st.begin());
+    double* dP = static_cast<double*>(st.dev(i_P));
+    double* dN = static_cast<double*>(st.scratch_ptr(k_next));
+    int* order = static_cast<int*>(st.scratch_ptr(k_order));
+    EACtrl* ctrl = static_cast<EACtrl*>(st.scratch_ptr(k_ctrl));
+    uint64_t* keys = static_cast<uint64_t*>(st.scratch_ptr(k_keys));
+    SBLM_CUDA(launch_rank(c, generation, static_cast<const double*>(st.dev(i_c)), dP,
+                          static_cast<sblm_ea_state*>(st.dev(i_s)), order, ctrl, keys, nullptr, true, s, n_pops));
+    SBLM_CUDA(launch_offspring(c, generation, dP, order, ctrl, keys, dN, s, n_pops));
+    SBLM_CUDA(cudaMemcpyAsync(dP, dN, sizeof(double) * all, cudaMemcpyDeviceToDevice, s));
     return st.end();
 }
 

@@ -115,6 +115,7 @@ _SIGS = {
     "sblm_ea_init": (ctypes.c_int, [_p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _p, _p]),
     "sblm_ea_generation": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_ea_generation_noalloc": (ctypes.c_int, [_p, _p, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
+    "sblm_ea_generation_batch": (ctypes.c_int, [_p, _p, _i32, _i32, _i32, ctypes.POINTER(EAParams), _u64, _i32, _p, _p]),
     "sblm_fit": (ctypes.c_int, [_p, _p, _p, _i32, ctypes.POINTER(Bounds), ctypes.POINTER(EAParams), _p, _p, _p, _p]),
     "sblm_peak_rates": (ctypes.c_int, [_p, _p, _p]),
     "sblm_fit_batch_tuned": (
@@ -358,6 +359,33 @@ def ea_generation(P, chi2_values, p, stream_id, generation, state, stream=None):
     s = _stream(stream, P, chi2_values, state)
     st = _lib.sblm_ea_generation(pp, pc, n_pop, n_par, ctypes.byref(p), stream_id, generation, ps, s)
     _check(st, "sblm_ea_generation")
+
+
+def ea_generation_batch(P, chi2_values, p, stream_id0, generation, states, stream=None):
+    """In place for n_pops populations at once: P [n_pops, n_pop, n_par] (or n_pops * n_pop rows with
+    p.n_pop rows each), chi2 [n_pops * n_pop], states [n_pops, state bytes] (device) or a list of
+    EAState (host, updated in place)."""
+    n_pop = int(p.n_pop)
+    n_rows, n_par = (int(P.shape[0]) * int(P.shape[1]), int(P.shape[2])) if P.ndim == 3 else (int(P.shape[0]),
+                                                                                            int(P.shape[1]))
+    if n_rows % n_pop:
+        raise ValueError("P must hold whole populations of p.n_pop rows")
+    n_pops = n_rows // n_pop
+    pp, _a = _ptr(P)
+    pc, _b = _ptr(chi2_values)
+    host_states = None
+    if isinstance(states, (list, tuple)):
+        host_states = states
+        buf = (EAState * n_pops)(*states)
+        ps, _c = ctypes.addressof(buf), buf
+    else:
+        ps, _c = _ptr(states)
+    s = _stream(stream, P, chi2_values, states if host_states is None else P)
+    st = _lib.sblm_ea_generation_batch(pp, pc, n_pops, n_pop, n_par, ctypes.byref(p), stream_id0, generation, ps, s)
+    _check(st, "sblm_ea_generation_batch")
+    if host_states is not None:
+        for k in range(n_pops):
+            ctypes.memmove(ctypes.addressof(host_states[k]), ctypes.addressof(buf[k]), ctypes.sizeof(EAState))
 
 
 def ea_generation_noalloc(P, chi2_values, p, stream_id, generation, state, stream=None):

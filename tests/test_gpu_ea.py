@@ -136,3 +136,29 @@ def test_fit_recovers_injected_event(lib):
     p = lib.params(n_pop=1024, n_gen=300, precision="mixed", seed=0)
     best, best_chi2 = lib.fit(lc.t, flux, sigma, synth.FIT_LO, synth.FIT_HI, p)
     assert best_chi2 - chi_true <= 1.0, (best, best_chi2, chi_true)
+
+
+@pytest.mark.parametrize("n_pops,n_pop,n_par", [(5, 64, 6), (3, 37, 5), (2, 1024, 6)])
+def test_batched_generation_equals_single_calls(lib, n_pops, n_pop, n_par):
+    """sblm_ea_generation_batch: n_pops populations in one launch per operator equal n_pops calls of
+    sblm_ea_generation with stream ids stream_id0 + b, over generations that include a restart
+    (constant fitness makes every generation stagnant)."""
+    p = lib.params(n_pop=n_pop, seed=11, restart_after=2, stag_window=2)
+    P0 = torch.empty((n_pops * n_pop, n_par), dtype=torch.float64, device="cuda")
+    states = torch.stack([lib.new_state_buffer("cuda") for _ in range(n_pops)])
+    for b in range(n_pops):
+        lib.ea_init(P0[b * n_pop : (b + 1) * n_pop], n_par, p, 4 + b, states[b])
+    Pb, sb = P0.clone(), states.clone()
+    Ps, ss = P0.clone(), states.clone()
+    g = np.random.default_rng(3)
+    for gen in range(7):
+        chi = g.uniform(0, 100, n_pops * n_pop) if gen % 3 else np.full(n_pops * n_pop, 5.0)
+        chi[::17] = np.nan
+        chi_d = dev(chi)
+        lib.ea_generation_batch(Pb, chi_d, p, 4, gen, sb)
+        for b in range(n_pops):
+            rows = slice(b * n_pop, (b + 1) * n_pop)
+            lib.ea_generation(Ps[rows], chi_d[rows], p, 4 + b, gen, ss[b])
+        assert torch.equal(Pb, Ps)
+        assert torch.equal(sb, ss)
+    assert any(lib.read_state(ss[b]).n_restarts > 0 for b in range(n_pops))
