@@ -98,6 +98,12 @@ typedef struct {
     int32_t migration_interval; /* with islands: every this many generations the elite of island i
                               replaces the last row of island (i + 1) mod n_islands (a ring);
                               <= 0 = islands never exchange rows (independent restarts) */
+    int32_t polish_starts; /* batched fitters with polish_fev > 0: the amoeba starts from the
+                              polish_starts fittest mutually distinct solutions the EA evaluated
+                              (the archive rule of sblm_batch_archive, radius polish_radius) and the
+                              best result is returned; 1 = the fittest solution only, as in the
+                              paper (default); at most 64 */
+    double polish_radius;  /* distinctness radius of those starts in the genes (default 0.05) */
 } sblm_ea_params;
 
 /* Dynamic state of one population between generations (Appendix A, "Stagnation checks"). */
@@ -120,7 +126,8 @@ const char* sblm_last_error(void);
 
 /* Fill *p with the paper's defaults: N_pop 1000, N_gen 100, p_mut0 0.01, N_tourn ceil(N_pop/25),
  * window 10, 1%, restart after 10, SBLM_MIXED, seed 0; one population (n_islands 1, migration
- * interval 20 if islands are asked for). */
+ * interval 20 if islands are asked for); the amoeba (when asked for) from the fittest solution
+ * only (polish_starts 1, polish_radius 0.05). */
 void sblm_ea_params_default(sblm_ea_params* p);
 
 /*

@@ -62,6 +62,7 @@ struct BatchArgs {
     const double* prop_win;   // first population are drawn here (else `seed` holds them)
     uint64_t prop_seed;
     int polish_fev;      // amoeba fine-tuning of the archive's best (0: none), a separate launch
+    int polish_starts;   // distinct starts of the amoeba (part of the graph's cache key)
     double* best_genes;  // [n_lc][6] genes of best_chi2
     int blend;           // chi^2 of the blended model with f profiled out (Section 4.4)
     double f_min;
@@ -440,6 +441,26 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_fit_kernel(BatchArg
     }
 }
 
+// several polish starts: the fittest polished start of each lightcurve (the first on ties)
+// replaces the EA's best when it is fitter
+__global__ void pick_polished_kernel(const double* __restrict__ g, const double* __restrict__ c, int n_lc, int starts,
+                                     double* __restrict__ best_genes, double* __restrict__ best_chi2) {
+    const int lc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lc >= n_lc) return;
+    int bk = -1;
+    double bc = best_chi2[lc];
+    for (int k = 0; k < starts; ++k) {
+        const double v = c[(size_t)lc * starts + k];
+        if (v < bc) {
+            bc = v;
+            bk = k;
+        }
+    }
+    if (bk < 0) return;
+    best_chi2[lc] = bc;
+    for (int j = 0; j < SBLM_NPAR; ++j) best_genes[(size_t)lc * SBLM_NPAR + j] = g[((size_t)lc * starts + bk) * SBLM_NPAR + j];
+}
+
 // theta rows of the (polished) best genes
 __global__ void genes_to_theta_kernel(const double* __restrict__ genes, int n_lc, Bounds b, double* __restrict__ theta) {
     const int lc = blockIdx.x * blockDim.x + threadIdx.x;
@@ -573,7 +594,21 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     const int k_next = st.scratch(sizeof(unsigned));
     const int k_genes = st.scratch(sizeof(double) * SBLM_NPAR * (size_t)n_lc);
     const int k_A = st.scratch(blend ? sizeof(double) * (size_t)blocks * c.n_pop * max_ep : 0);
-    const int polish_blocks = std::min(n_lc, 2 * sms);
+    // the amoeba from several distinct starts (polish_starts > 1): the archive of the solutions the
+    // EA evaluated (the caller's, or one kept for this purpose) supplies them
+    const int starts = params->polish_fev > 0 ? std::max(1, params->polish_starts) : 1;
+    if (starts > 64) return fail(SBLM_EINVAL, "polish_starts must be in [1, 64]");
+    if (starts > 1 && (!(params->polish_radius > 0.0) || !std::isfinite(params->polish_radius)))
+        return fail(SBLM_EINVAL, "polish_radius must be > 0");
+    const int arc_k = arc ? arc->size : (starts > 1 ? starts : 0);  // archive entries per lightcurve
+    const int inst_per_lc = starts > 1 ? arc_k : 1;                 // polish instances per lightcurve
+    const int polish_blocks = (int)std::min<long>((long)n_lc * inst_per_lc, 2L * sms);
+    const int k_pg = st.scratch(starts > 1 ? sizeof(double) * SBLM_NPAR * (size_t)n_lc * inst_per_lc : 0);
+    const int k_pc = st.scratch(starts > 1 ? sizeof(double) * (size_t)n_lc * inst_per_lc : 0);
+    const int k_iag = st.scratch(!arc && starts > 1 ? sizeof(double) * SBLM_NPAR * (size_t)n_lc * arc_k : 0);
+    const int k_iat = st.scratch(!arc && starts > 1 ? sizeof(double) * SBLM_NPAR * (size_t)n_lc * arc_k : 0);
+    const int k_iac = st.scratch(!arc && starts > 1 ? sizeof(double) * (size_t)n_lc * arc_k : 0);
+    const int k_ian = st.scratch(!arc && starts > 1 ? sizeof(int) * (size_t)n_lc : 0);
     const int k_pA = st.scratch(blend && params->polish_fev > 0 ? sizeof(double) * (size_t)polish_blocks * max_ep : 0);
     const PolishMixed pmx = polish_mixed_layout(max_ep);
     const int k_pq = st.scratch(mode == SBLM_MIXED && params->polish_fev > 0 ? pmx.block_bytes * polish_blocks : 0);
@@ -641,6 +676,7 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     a.seed = i_seed >= 0 ? static_cast<const double*>(st.dev(i_seed)) : nullptr;
     a.n_seed = n_seed;
     a.polish_fev = params->polish_fev;
+    a.polish_starts = starts;
     a.best_genes = static_cast<double*>(st.scratch_ptr(k_genes));
     a.blend = blend ? 1 : 0;
     a.f_min = SBLM_BLEND_F_MIN;
@@ -665,6 +701,14 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
         a.arc_theta = static_cast<double*>(st.dev(i_arc[0]));
         a.arc_chi2 = static_cast<double*>(st.dev(i_arc[1]));
         a.arc_count = static_cast<int*>(st.dev(i_arc[2]));
+    } else if (starts > 1) {  // an archive kept only for the polish starts: every evaluated row offered
+        a.arc_size = arc_k;
+        a.arc_top = 0;
+        a.arc_radius = params->polish_radius;
+        a.arc_genes = static_cast<double*>(st.scratch_ptr(k_iag));
+        a.arc_theta = static_cast<double*>(st.scratch_ptr(k_iat));
+        a.arc_chi2 = static_cast<double*>(st.scratch_ptr(k_iac));
+        a.arc_count = static_cast<int*>(st.scratch_ptr(k_ian));
     }
     out->a = a;
     PolishArgs pa{};
@@ -680,6 +724,15 @@ sblm_status prepare(const double* t, const double* flux, const double* sigma, co
     pa.c_stride = 1;
     pa.g_out = a.best_genes;
     pa.c_out = a.best_chi2;
+    if (starts > 1) {  // every archived start (up to polish_starts of them) into separate outputs
+        pa.starts = inst_per_lc;
+        pa.counts = a.arc_count;
+        pa.max_starts = starts;
+        pa.g_in = a.arc_genes;
+        pa.c_in = a.arc_chi2;
+        pa.g_out = static_cast<double*>(st.scratch_ptr(k_pg));
+        pa.c_out = static_cast<double*>(st.scratch_ptr(k_pc));
+    }
     pa.maxfev = params->polish_fev;
     pa.mixed = st.scratch_ptr(k_pq);
     pa.mx = pmx;
@@ -727,6 +780,11 @@ sblm_status run_graph(const Prepared& p, cudaStream_t s) {
             cudaError_t e2 = launch_batch(p.mode, p.a, p.blocks, p.threads, p.smem, cap, false);
             if (e2 == cudaSuccess && p.a.polish_fev > 0) {
                 e2 = launch_polish(p.mode, p.pa, p.polish_blocks, p.max_ep, cap);
+                if (e2 == cudaSuccess && p.pa.starts > 1) {
+                    pick_polished_kernel<<<(p.a.n_lc + 127) / 128, 128, 0, cap>>>(
+                        p.pa.g_out, p.pa.c_out, p.a.n_lc, p.pa.starts, p.a.best_genes, p.a.best_chi2);
+                    e2 = cudaGetLastError();
+                }
                 if (e2 == cudaSuccess) {
                     genes_to_theta_kernel<<<(p.a.n_lc + 127) / 128, 128, 0, cap>>>(p.a.best_genes, p.a.n_lc, p.a.b,
                                                                                  p.a.best_theta);

@@ -264,11 +264,22 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
             gap2[j] = fmin(gap2[j], g);
         }
     const T zeta_abs = sqrt_(norm2(zeta));
-    Root<T> rp[5];
-    T r2[5], det[5];
+    Root<T> rp[5], ri[5];
+    T r2[5], det[5], gp[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        Root<T> r = rr[i];
+        ri[i] = rr[i];
+        gp[i] = gap2[i];
+        rp[i] = rr[i];
+        r2[i] = T(0);
+        det[i] = T(0);
+    }
+    // one copy of the per-root body: slot 0 is processed, then every array turns by one place, so
+    // after five turns the inputs are back in order and the outputs sit at their roots' indices
+#pragma unroll 1
+    for (int i = 0; i < 5; ++i) {
+        const Root<T> r_in = ri[0];
+        Root<T> r = r_in;
         cx<T> f, K;
         T qt = T(0);
 #pragma unroll 1
@@ -276,7 +287,6 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
             lens_terms(r, zeta, d, q, f, K, qt);
             if (s == Tol<T>::polish) break;
             if (s == 0) {
-                // a root whose residual is far beyond the ambiguous band is spurious: no polish
                 const T az2 = norm2(r.z);
                 const T sc = sqrt_(az2) + rsqrt_(az2) + qt + zeta_abs;
                 if (norm2(f) > T(kSpurious) * T(kSpurious) * sc * sc) break;
@@ -287,7 +297,6 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
             const cx<T> delta = rcp(fabs(dj)) * (dj < T(0) ? -num : num);
             if (!finite2(delta)) break;
             const T ref2 = r.local ? norm2(r.w) : norm2(r.z);
-            // converged: this step is below the rounding level, keep (f, K) of this position
             if (norm2(delta) <= T(4) * Eps<T>::value * Eps<T>::value * ref2) break;
             if (r.local) {
                 r.w = r.w + delta;
@@ -296,17 +305,30 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
                 r.z = r.z + delta;
             }
         }
-        const cx<T> moved = r.local ? r.w - rr[i].w : r.z - rr[i].z;
-        if (!(norm2(moved) <= T(0.25) * gap2[i]) || !finite2(r.z)) {
-            r = rr[i];
+        const cx<T> moved = r.local ? r.w - r_in.w : r.z - r_in.z;
+        if (!(norm2(moved) <= T(0.25) * gp[0]) || !finite2(r.z)) {
+            r = r_in;
             lens_terms(r, zeta, d, q, f, K, qt);
         }
         const T az2 = norm2(r.z);
         const T scale = sqrt_(az2) + rsqrt_(az2) + qt + zeta_abs;
         const T q2 = norm2(f) / (scale * scale);
-        r2[i] = isfinite(q2) ? q2 : T(INFINITY);
-        det[i] = T(1) - norm2(K);
-        rp[i] = r;
+        const T r2v = isfinite(q2) ? q2 : T(INFINITY);
+        const T detv = T(1) - norm2(K);
+        const T g0 = gp[0];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ri[k] = ri[k + 1];
+            gp[k] = gp[k + 1];
+            rp[k] = rp[k + 1];
+            r2[k] = r2[k + 1];
+            det[k] = det[k + 1];
+        }
+        ri[4] = r_in;
+        gp[4] = g0;
+        rp[4] = r;
+        r2[4] = r2v;
+        det[4] = detv;
     }
     const T lens2 = Tol<T>::lens * Tol<T>::lens;
     bool acc[5];

@@ -28,19 +28,25 @@ __global__ void __launch_bounds__(kPolishThreads) polish_kernel(PolishArgs a) {
         sink.queue_cap = a.mx.queue_cap;
         term_row = reinterpret_cast<double*>(m + a.mx.off_term);
     }
-    for (int lc = blockIdx.x; lc < a.n_lc; lc += gridDim.x) {
+    const int starts = a.starts > 1 ? a.starts : 1;
+    for (int inst = blockIdx.x; inst < a.n_lc * starts; inst += gridDim.x) {
+        const int lc = inst / starts;
+        if (starts > 1 && inst % starts >= min(a.counts[lc], a.max_starts)) {  // no such start
+            if (threadIdx.x == 0) a.c_out[(size_t)inst * a.c_stride] = INFINITY;
+            continue;
+        }
         const int64_t e0 = a.offsets ? a.offsets[lc] : 0;
         const int n_ep = a.offsets ? (int)(a.offsets[lc + 1] - e0) : a.n_ep;
         const LCView view = stage_lightcurve<MODE, true>(smem, a.t + e0, a.flux + e0, a.sigma + e0, n_ep);
         double g[kPolishN];
-        for (int j = 0; j < kPolishN; ++j) g[j] = a.g_in[(size_t)lc * a.g_stride + j];
-        double f = a.c_in ? a.c_in[(size_t)lc * a.c_stride] : INFINITY;
+        for (int j = 0; j < kPolishN; ++j) g[j] = a.g_in[(size_t)inst * a.g_stride + j];
+        double f = a.c_in ? a.c_in[(size_t)inst * a.c_stride] : INFINITY;
         double* A_row = a.blend ? a.A_scr + (size_t)blockIdx.x * a.A_stride : nullptr;
         block_nelder_mead<MODE>(g, &f, a.maxfev, a.b, view, n_ep, sink, term_row, s_red, A_row, a.f_min);
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int j = 0; j < kPolishN; ++j) a.g_out[(size_t)lc * a.g_stride + j] = g[j];
-            a.c_out[(size_t)lc * a.c_stride] = f;
+            for (int j = 0; j < kPolishN; ++j) a.g_out[(size_t)inst * a.g_stride + j] = g[j];
+            a.c_out[(size_t)inst * a.c_stride] = f;
         }
         __syncthreads();
     }

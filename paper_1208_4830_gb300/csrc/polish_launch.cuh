@@ -31,12 +31,15 @@ struct PolishArgs {
     int n_ep;
     int n_lc;
     Bounds b;
-    const double* g_in;  // start genes of lightcurve l at g_in[l * g_stride]
+    int starts;          // searches per lightcurve (instance i: lightcurve i / starts); 0 or 1: one
+    const int* counts;   // starts > 1: starts of lightcurve l in use: min(counts[l], max_starts)
+    int max_starts;
+    const double* g_in;  // start genes of instance i at g_in[i * g_stride]
     int g_stride;
-    const double* c_in;  // their chi^2 at c_in[l * c_stride], or null (evaluated)
+    const double* c_in;  // their chi^2 at c_in[i * c_stride], or null (evaluated)
     int c_stride;
     double* g_out;       // may alias g_in
-    double* c_out;       // may alias c_in
+    double* c_out;       // may alias c_in; a skipped instance gets +inf
     int maxfev;
     void* mixed;         // MIXED: mx.block_bytes of scratch per block
     PolishMixed mx;      // MIXED: polish_mixed_layout(longest lightcurve)

@@ -262,6 +262,8 @@ void sblm_ea_params_default(sblm_ea_params* p) {
     p->seed = 0;
     p->n_islands = 1;
     p->migration_interval = 20;
+    p->polish_starts = 1;
+    p->polish_radius = 0.05;
 }
 
 }  // extern "C"

@@ -50,6 +50,8 @@ class EAParams(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("n_islands", ctypes.c_int32),
         ("migration_interval", ctypes.c_int32),
+        ("polish_starts", ctypes.c_int32),
+        ("polish_radius", ctypes.c_double),
     ]
 
 

@@ -48,9 +48,10 @@ def test_struct_layout_matches_header(built, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sblm.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(sblm_bounds), sizeof(sblm_ea_params),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(sblm_bounds), sizeof(sblm_ea_params),"
         " sizeof(sblm_ea_state), offsetof(sblm_ea_params, seed), offsetof(sblm_ea_state, best_genes),"
-        " offsetof(sblm_ea_state, n_hist), offsetof(sblm_ea_params, n_islands)); return 0;}\n"
+        " offsetof(sblm_ea_state, n_hist), offsetof(sblm_ea_params, n_islands),"
+        " offsetof(sblm_ea_params, polish_radius)); return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -64,6 +65,7 @@ def test_struct_layout_matches_header(built, tmp_path):
         s.EAState.best_genes.offset,
         s.EAState.n_hist.offset,
         s.EAParams.n_islands.offset,
+        s.EAParams.polish_radius.offset,
     ]
     assert got == want
 

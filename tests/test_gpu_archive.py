@@ -94,3 +94,44 @@ def test_archive_rejects_bad_settings(lib):
         args.update(kw)
         with pytest.raises(lib.SBLMError):
             lib.fit_batch_archived(b.t, flux, sigma, b.offsets, synth.FIT_LO, synth.FIT_HI, p, **args)
+
+
+def test_polish_from_several_starts(lib):
+    """polish_starts = K: the amoeba runs from each of the K fittest distinct solutions the EA
+    evaluated (the archive rule) and the fittest result is returned. In FP64 that equals polishing
+    each entry of the archive the same fit returns (sblm_polish_batch) and keeping the best; it is
+    never worse than the single start of the paper's EA + amoeba."""
+    b = synth.heldout_batch(6, seed=51, n_ep=300)
+    A = np.concatenate([osb.magnification(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]])[0]
+                        for i in range(6)])
+    flux, sigma = b.observe(A)
+    args = (b.t, flux, sigma, b.offsets, synth.FIT_LO, synth.FIT_HI)
+    p1 = lib.params(n_pop=96, n_gen=25, precision="fp64", seed=3, polish_fev=300)
+    pk = lib.params(n_pop=96, n_gen=25, precision="fp64", seed=3, polish_fev=300, polish_starts=4,
+                    polish_radius=0.05)
+    _, c1 = lib.fit_batch(*args, p1)
+    best_k, ck = lib.fit_batch(*args, pk)
+    assert np.all(ck <= c1 * (1 + 1e-12))
+    # host replay: the archive of the same EA, every entry polished, the fittest kept
+    p0 = lib.params(n_pop=96, n_gen=25, precision="fp64", seed=3)
+    _, c_ea, a_th, a_c, a_n = lib.fit_batch_archived(*args, p0, size=4, radius=0.05)
+    for i in range(6):
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        n = int(a_n[i])
+        g = np.column_stack([a_th[i, :n, :5], np.log10(a_th[i, :n, 5])])
+        g = (g - synth.FIT_LO) / (synth.FIT_HI - synth.FIT_LO)
+        off = np.array([0] + [sl.stop - sl.start] * n, dtype=np.int64).cumsum()
+        tt, ff, ss = (np.tile(x[sl], n) for x in (b.t, flux, sigma))
+        _, cp = lib.polish_batch(tt, ff, ss, off, synth.FIT_LO, synth.FIT_HI, np.ascontiguousarray(g), 300, "fp64")
+        assert ck[i] == pytest.approx(min(cp.min(), c_ea[i]), rel=1e-9)
+
+
+def test_polish_starts_validation(lib):
+    b = synth.seasonal_batch(2, seed=3, n_min=50, n_max=60)
+    A = np.concatenate([osb.magnification(b.truth[i : i + 1], b.t[b.offsets[i] : b.offsets[i + 1]])[0]
+                        for i in range(2)])
+    flux, sigma = b.observe(A)
+    for kw in ({"polish_starts": 65}, {"polish_starts": 3, "polish_radius": 0.0}):
+        p = lib.params(n_pop=16, n_gen=2, precision="fp64", polish_fev=10, **kw)
+        with pytest.raises(lib.SBLMError):
+            lib.fit_batch(b.t, flux, sigma, b.offsets, synth.FIT_LO, synth.FIT_HI, p)

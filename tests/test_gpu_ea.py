@@ -131,9 +131,11 @@ def test_fit_trace_and_result_consistent(lib, prec):
 
 
 def test_fit_recovers_injected_event(lib):
-    """Recovery of the single-lightcurve event, judged by delta chi^2 <= 1 against the truth."""
+    """Recovery of the single-lightcurve event, judged by delta chi^2 <= 1 against the truth: the EA
+    with the amoeba of Section 4.1 (without it the EA alone stopped at delta chi^2 = 2.5 next to the
+    truth in one build: its last digits are not converged by a generation budget)."""
     lc, flux, sigma, chi_true = _config1()
-    p = lib.params(n_pop=1024, n_gen=300, precision="mixed", seed=0)
+    p = lib.params(n_pop=1024, n_gen=300, precision="mixed", seed=0, polish_fev=2000)
     best, best_chi2 = lib.fit(lc.t, flux, sigma, synth.FIT_LO, synth.FIT_HI, p)
     assert best_chi2 - chi_true <= 1.0, (best, best_chi2, chi_true)
 
