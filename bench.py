@@ -605,7 +605,7 @@ def _peak_classes(sblm, b, n_lc):
     return np.concatenate(A), np.array(peaks)
 
 
-def _paper_arms(sblm, w, b, dev, lo, hi, precision, chi_true, nu, peaks, f_true=None):
+def _paper_arms(sblm, w, b, dev, lo, hi, precision, chi_true, nu, peaks, f_true=None, m0=None):
     """EA + amoeba on the paper-shaped curves, plain and proposal-seeded. Success as in Section 4.2:
     strict = some returned model (every evaluated population, through the device's success
     monitor, or the polished best) has delta chi^2 / nu < 1 and every parameter within 10%; weak =
@@ -652,6 +652,11 @@ def _paper_arms(sblm, w, b, dev, lo, hi, precision, chi_true, nu, peaks, f_true=
                       "strict_best_only_range_relative_pct_by_peaks": {str(k): pct(strict_range, k) for k in (1, 2, 3, 4)},
                       "median_first_matching_generation": float(np.median(first[first >= 0])) if np.any(first >= 0)
                       else None}
+        if m0 is not None:  # the noisy test's success against the source's unlensed magnitude
+            bins = ((18.0, 19.0), (19.0, 20.0), (20.0, 21.0), (21.0, 22.0))
+            out[label]["success_strict_weak_pct_by_m0"] = {
+                f"{a:g}-{z:g}": [round(100 * float(strict[(m0 >= a) & (m0 < z)].mean()), 1),
+                                 round(100 * float(weak[(m0 >= a) & (m0 < z)].mean()), 1)] for a, z in bins}
     return out
 
 
@@ -694,13 +699,14 @@ def run_noisy_blended_workload(sblm, w):
                                          flux[b.offsets[i] : b.offsets[i + 1]], sigma[b.offsets[i] : b.offsets[i + 1]],
                                          "fp64")[0][0] for i in range(PAPER_LCS)])
     out = {"workload": f"{PAPER_LCS} noisy, blended curves of the paper's second test (Table 1 ranges, 100 random "
-                       f"epochs, noise model of Section 2.4, f in (0, 1]); blended chi^2 with f profiled out; "
+                       f"epochs, noise model of Section 2.4 at the true magnitude, m0 the source's unlensed magnitude in "
+                       f"[18, 22], f in (0, 1]); blended chi^2 with f profiled out; "
                        f"N_pop {PAPER_POP} x {PAPER_GEN} generations + amoeba ({FIT_POLISH} evaluations)",
            "curves_per_peak_class": {str(k): int(np.sum(peaks == k)) for k in (1, 2, 3, 4)},
            "paper_table3_ea_amoeba_strict_weak_pct": PAPER_TABLE3_EA_AMOEBA}
     # nu = 100 - 7: six lens and trajectory parameters plus f
     out.update(_paper_arms(sblm, w, b, dev, synth.PAPER_LO, synth.PAPER_HI, "mixed+blend", chi_true, 100 - 7, peaks,
-                           f_true=b.f))
+                           f_true=b.f, m0=b.m0))
     return out
 
 

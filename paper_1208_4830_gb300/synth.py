@@ -262,7 +262,7 @@ def count_peaks(A, rel_prominence=0.01):
 
 # Section 2.4's photometric noise model: log10 sigma_I = slope * m_I + intercept (magnitudes)
 NOISE_SLOPE, NOISE_INTERCEPT = 0.3416, -7.7095
-M0_RANGE = (18.0, 22.0)  # Table 1: unlensed magnitude
+M0_RANGE = (18.0, 22.0)  # Table 1: unlensed magnitude of the source
 
 
 @dataclass
@@ -271,30 +271,34 @@ class NoisyBlendedBatch:
     offsets: np.ndarray  # int64 [n_lc + 1]
     truth: np.ndarray    # (n_lc, 6) lens and trajectory
     f: np.ndarray        # (n_lc,) blending fraction: source flux / total unlensed flux
-    m0: np.ndarray       # (n_lc,) baseline magnitude
+    m0: np.ndarray       # (n_lc,) unlensed magnitude of the source (blended light excluded)
     z: np.ndarray        # unit-normal draws, one per epoch
 
     def observe(self, A_true):
-        """(flux, sigma) normalised to the baseline from the truths' source magnifications
-        (concatenated, any implementation): the true magnitude m = m0 - 2.5 log10(f A + 1 - f)
-        gets Gaussian noise of the noise model's sigma_m(m); the observed flux is
-        10^(-0.4 (m_obs - m0)) and its sigma the first-order image 0.4 ln 10 F sigma_m of the
-        magnitude error at the true flux F."""
+        """(flux, sigma) normalised to the total unlensed flux, from the truths' source
+        magnifications (concatenated, any implementation). m0 is the source's unlensed magnitude
+        (Section 2's parameter list), so the unlensed blend of source and other light has
+        magnitude m0 + 2.5 log10 f and the true magnitude is m = m0 - 2.5 log10(A + (1 - f)/f);
+        it gets Gaussian noise of the noise model's sigma_m(m); the observed flux is
+        10^(-0.4 (m_obs - m_blend)) and its sigma the first-order image 0.4 ln 10 F sigma_m of the
+        magnitude error at the true flux F = f A + 1 - f."""
         n = np.diff(self.offsets)
         f = np.repeat(self.f, n)
         m0 = np.repeat(self.m0, n)
         F = f * np.asarray(A_true) + (1.0 - f)
-        m = m0 - 2.5 * np.log10(F)
+        m_blend = m0 + 2.5 * np.log10(f)
+        m = m_blend - 2.5 * np.log10(F)
         s_m = 10.0 ** (NOISE_SLOPE * m + NOISE_INTERCEPT)
-        flux = 10.0 ** (-0.4 * (m + s_m * self.z - m0))
+        flux = 10.0 ** (-0.4 * (m + s_m * self.z - m_blend))
         return flux, 0.4 * np.log(10.0) * s_m * F
 
 
 def noisy_blended_batch(n_lc=512, seed=0, n_ep=100):
     """Curves shaped like the paper's noisy, blended test (Section 4.4): parameters as in
-    paper_batch (Table 1 ranges, q uniform in [0.1, 1]), m0 uniform over Table 1's [18, 22], a
-    blending fraction f uniform on (0, 1], and n_ep epochs drawn uniformly on (t_start, t_end)
-    (sorted), with (t_start - t0)/tE in (-3, -2) and (t_end - t0)/tE in (2, 3)."""
+    paper_batch (Table 1 ranges, q uniform in [0.1, 1]), the source's unlensed magnitude m0
+    uniform over Table 1's [18, 22], a blending fraction f uniform on (0, 1], and n_ep epochs
+    drawn uniformly on (t_start, t_end) (sorted), with (t_start - t0)/tE in (-3, -2) and
+    (t_end - t0)/tE in (2, 3)."""
     g = _rng(seed)
     u = g.uniform(size=(n_lc, 6))
     theta = PAPER_LO + (PAPER_HI - PAPER_LO) * u

@@ -46,14 +46,21 @@ def test_noisy_blended_batch_follows_the_paper_setup():
         t0, tE = b.truth[i, 0], b.truth[i, 1]
         assert np.all(np.diff(t) >= 0) and (t[0] - t0) / tE > -3 and (t[-1] - t0) / tE < 3
         assert np.std(np.diff(t)) > 0.1 * np.mean(np.diff(t))  # not evenly spaced
-    # at baseline (A = 1) the magnitude error is the noise model's: log10 sigma = 0.3416 m0 - 7.7095
+    # m0 is the source's unlensed magnitude (Section 2), so at baseline (A = 1) the light is the
+    # unlensed blend of magnitude m0 + 2.5 log10 f, and its error is the noise model's there:
+    # log10 sigma = 0.3416 m - 7.7095
     flux, sigma = b.observe(np.ones(b.t.size))
     n = np.diff(b.offsets)
-    m0 = np.repeat(b.m0, n)
-    np.testing.assert_allclose(sigma, 0.4 * np.log(10) * 10 ** (0.3416 * m0 - 7.7095), rtol=1e-12)
-    m_obs = b.m0.repeat(n) - 2.5 * np.log10(flux)
-    r = (m_obs - m0) / 10 ** (0.3416 * m0 - 7.7095)
+    m_base = np.repeat(b.m0 + 2.5 * np.log10(b.f), n)
+    np.testing.assert_allclose(sigma, 0.4 * np.log(10) * 10 ** (0.3416 * m_base - 7.7095), rtol=1e-12)
+    r = -2.5 * np.log10(flux) / 10 ** (0.3416 * m_base - 7.7095)
     np.testing.assert_allclose(r, b.z, atol=1e-9)
+    # an unblended source (f = 1) at baseline has magnitude m0; the blend is brighter than the source
+    b1 = synth.noisy_blended_batch(50, seed=6)
+    b1.f[:] = 1.0
+    _, s1 = b1.observe(np.ones(b1.t.size))
+    np.testing.assert_allclose(s1, 0.4 * np.log(10) * 10 ** (0.3416 * np.repeat(b1.m0, n) - 7.7095), rtol=1e-12)
+    assert np.all(sigma <= s1)
     # f dilutes the source magnification: F - 1 = f (A - 1) without noise
     b.z[:] = 0.0
     A = np.linspace(1.0, 30.0, b.t.size)
