@@ -151,3 +151,15 @@ def test_operation_count_per_magnification(loop):
     assert n == rows.size * 1000
     assert 1500 < f32_long / n < f32_short / n < 5000
     assert deferred > 0 and 500 < f64 / deferred < 10000
+
+
+def test_cyclic_aberth_equals_the_sweep_form(loop):
+    """The library's Aberth loop visits only the roots that are not done, in cyclic order, turning
+    the root array in registers; the textbook Gauss-Seidel form (sweeps over roots 0..4 that skip
+    finished roots) takes the same updates in the same order. On 40,000 random quintics (FP32 and
+    FP64, cold and warm starts, partial active masks, caps of 1 to 3 sweeps that fail) both return
+    the same roots and sweep counts bit for bit (contraction off)."""
+    wd, _ = loop
+    cases, bad, capped, masked = host_build.aberth_order(wd)
+    assert cases == 40000 and bad == 0
+    assert capped > 1000 and masked > 1000
