@@ -211,7 +211,10 @@ __device__ __forceinline__ double eval_run(const Cand& k, bool valid, int c_tag,
                         } else {  // queue full: re-solve here, from the FP64 data
                             const double te = lc.t[e];
                             const double fe = CHI2 ? lc.flux[e] : 0.0, we = CHI2 ? 1.0 / lc.sigma[e] : 0.0;
-                            const double tm = resolve_fp64(z, why, &k, te, fe, we, A_row, f_row, e, CHI2);
+                            cx<float> zc[5];  // a copy, so that z's address is never taken and z stays in registers
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) zc[i] = z[i];
+                            const double tm = resolve_fp64(zc, why, &k, te, fe, we, A_row, f_row, e, CHI2);
                             if (CHI2) term_row[e] = tm;
                         }
                     }

@@ -1,9 +1,10 @@
-// The library's Aberth iteration (forward.cuh: aberth, which visits the roots that are not done in
-// cyclic order and turns the root array in registers) against the textbook form of the same
-// Gauss-Seidel iteration written here with plain indexing: sweeps over roots 0..4 that skip the
-// roots already done, ending after the first sweep in which every visited root finished, or
-// failing after `cap` sweeps. Both take the same updates in the same order, so with contraction
-// off the roots and the returned sweep counts must agree bit for bit. Test infrastructure.
+// The library's Aberth iteration (forward.cuh: aberth, one copy of the per-root body that always
+// updates z[0] and then turns the root array by one place, so that a sweep is five turns) against
+// the textbook form of the same Gauss-Seidel iteration written here with plain indexing: sweeps over
+// roots 0..4 that skip the roots already done, ending after the first sweep in which every visited
+// root finished, or failing after `cap` sweeps. Both take the same updates in the same order, so
+// with contraction off the roots and the returned sweep counts must agree bit for bit. Test
+// infrastructure.
 //
 // Output: cases, mismatches, cases that hit the cap, cases with a partial active mask.
 #include <cstdio>

@@ -2,7 +2,7 @@
 
 ``csrc/common.cuh`` and ``csrc/forward.cuh`` are copied with their device qualifiers dropped and
 the few device intrinsics replaced by host arithmetic: the hardware reciprocal approximation by
-an IEEE division, the fast exp/log by expf/logf, popc and ffs by the compiler builtins; products are
+an IEEE division, the fast exp/log by expf/logf, popc by the compiler builtin; products are
 contracted into fused multiply-adds as nvcc does. The result models the device's FP32 epoch
 loop closely enough to check its logic (root iteration, image selection, the MIXED triggers) on
 a CPU; on the 4096 x 2000 sweep it reproduced the device's re-solve flags and failing epochs.
@@ -31,7 +31,7 @@ def _host(src: str) -> str:
     src = re.sub(r'asm\("rcp\.approx\.ftz\.f32 %0, %1;" : "=f"\(r\) : "f"\(x\)\);', "r = 1.0f / x;", src)
     src = re.sub(r'asm\("rcp\.approx\.ftz\.f64 %0, %1;" : "=d"\(r\) : "d"\(x\)\);', "r = 1.0 / x;", src)
     src = src.replace("rsqrtf(x)", "(1.0f / sqrtf(x))").replace("return rsqrt(x);", "return 1.0 / sqrt(x);")
-    src = src.replace("__expf", "expf").replace("__logf", "logf").replace("__popc(", "__builtin_popcount(").replace("__ffs(", "__builtin_ffs(")
+    src = src.replace("__expf", "expf").replace("__logf", "logf").replace("__popc(", "__builtin_popcount(")
     src = src.replace("__umul64hi(", "umul64hi_host(")
     return src
 

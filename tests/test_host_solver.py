@@ -153,12 +153,13 @@ def test_operation_count_per_magnification(loop):
     assert deferred > 0 and 500 < f64 / deferred < 10000
 
 
-def test_cyclic_aberth_equals_the_sweep_form(loop):
-    """The library's Aberth loop visits only the roots that are not done, in cyclic order, turning
-    the root array in registers; the textbook Gauss-Seidel form (sweeps over roots 0..4 that skip
-    finished roots) takes the same updates in the same order. On 40,000 random quintics (FP32 and
-    FP64, cold and warm starts, partial active masks, caps of 1 to 3 sweeps that fail) both return
-    the same roots and sweep counts bit for bit (contraction off)."""
+def test_rolled_aberth_equals_the_sweep_form(loop):
+    """The library's Aberth loop is one copy of the per-root body that updates z[0] and turns the
+    root array by one place (five turns make a sweep, done bits turning with the roots); the
+    textbook Gauss-Seidel form indexes the roots directly (sweeps over roots 0..4 that skip finished
+    roots). On 40,000 random quintics (FP32 and FP64, cold and warm starts, partial active masks,
+    caps of 1 to 3 sweeps that fail) both return the same roots and sweep counts bit for bit
+    (contraction off)."""
     wd, _ = loop
     cases, bad, capped, masked = host_build.aberth_order(wd)
     assert cases == 40000 and bad == 0
