@@ -50,11 +50,10 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # operation the algorithm performs as written, a fused multiply-add counted as 2); see
 # profiles/forward_kernel_mixed_sweep_32x4096x2000.md
 # (python tests/host_solver/count_workload.py --stride 16 --seg 250: 8192 of the 131072 candidates, every
-# epoch; 0.347% of the epochs re-solved in FP64, 3075 FP64 operations each). traffic: DRAM bytes
+# epoch; 0.341% of the epochs re-solved in FP64, 3087 FP64 operations each). traffic: DRAM bytes
 # read + written per forward_kernel launch of the full step, from an ncu capture of 20 populations
-# scaled by the magnifications (the dense term rows, 8 B per magnification, dominate); None until
-# the current kernel has been captured
-FLOP_COUNT = {"mixed": {"fp32_per_mag": 2380.9, "fp64_per_mag": 10.68, "traffic": None,
+# scaled by the magnifications (the dense term rows, 8 B per magnification, dominate)
+FLOP_COUNT = {"mixed": {"fp32_per_mag": 2387.8, "fp64_per_mag": 10.51, "traffic": 2.77e9,
                         "file": "profiles/forward_kernel_mixed_sweep_32x4096x2000.md"}}
 
 

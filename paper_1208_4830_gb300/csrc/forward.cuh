@@ -17,21 +17,24 @@ namespace sblm {
 // a root whose residual lies between `lens` and this is neither clearly an image nor clearly
 // spurious (an image pair the arithmetic could not resolve drops out with opposite parities,
 // leaving the count and parity tests satisfied), so the epoch is flagged. `polish`: most Newton
-// steps per root (fewer once a step is below the rounding level). `cubic`: a root whose Aberth
-// correction is below this (relative) is done: the iteration converges cubically, so after that
-// update its error is far below the lens-equation polish's reach.
+// steps per root (fewer once a step is below the rounding level). `stall`: the polish also stops
+// when a step left the squared residual above this fraction of the previous one (0: never), i.e.
+// once the residual is at FP32's rounding level and Newton's steps only move the root within it.
+// `cubic`: a root whose Aberth correction is below this (relative) is done: the iteration
+// converges cubically, so after that update its error is far below the lens-equation polish's
+// reach.
 template <typename T>
 struct Tol;
 template <>
 struct Tol<double> {
     static constexpr double step = 1e-13, lens = 1e-10, pair = 1e-8, dup = 1e-9, shift = 1e-12, ambiguous = 0.0,
-                            cubic = 1e-13;
+                            cubic = 1e-13, stall = 0.0;
     static constexpr int cap_cold = 120, cap_warm = 40, polish = 2;
 };
 template <>
 struct Tol<float> {
     static constexpr float step = 2e-6f, lens = 2e-6f, pair = 2e-5f, dup = 1e-5f, shift = 1e-6f, ambiguous = 3e-3f,
-                           cubic = 1e-3f;
+                           cubic = 1e-3f, stall = 0.81f;
     static constexpr int cap_cold = 100, cap_warm = 30, polish = 4;
 };
 
@@ -242,9 +245,10 @@ constexpr float kSpurious = 0.05f;
 constexpr float kSpuriousPair = 0.25f;
 
 // Spurious-root rejection (Section 2.2: substitution into Eq. (lensing)) and magnification.
-// Each root gets `polish` Newton steps on the lens equation itself,
+// Each root gets up to `polish` Newton steps on the lens equation itself,
 //   delta = (-f + K conj(f)) / (1 - |K|^2),
-// and keeps its unpolished value if that moved it by more than half its distance to the
+// (fewer once a step is below the rounding level or the residual stalls, Tol::stall) and keeps its
+// unpolished value if that moved it by more than half its distance to the
 // nearest other root. Images: relative residual |f| / (|z| + 1/|z| + q/|d - z| + |zeta|) at
 // most Tol::lens; the count must be 3 or 5, the parities (sign of det J) must sum to -1 and no
 // two images may coincide; otherwise the 3 smallest residuals are taken, plus the 4th and 5th
@@ -281,7 +285,7 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
         const Root<T> r_in = rp[0];
         Root<T> r = r_in;
         cx<T> f, K;
-        T qt = T(0);
+        T qt = T(0), f2prev = T(INFINITY);
 #pragma unroll 1
         for (int s = 0; s <= Tol<T>::polish; ++s) {
             lens_terms(r, zeta, d, q, f, K, qt);
@@ -290,6 +294,11 @@ __device__ __forceinline__ EpochOut<T> select_images(const Root<T> rr[5], cx<T> 
                 const T az2 = norm2(r.z);
                 const T sc = sqrt_(az2) + rsqrt_(az2) + qt + zeta_abs;
                 if (norm2(f) > T(kSpurious) * T(kSpurious) * sc * sc) break;
+            }
+            if (Tol<T>::stall > T(0)) {
+                const T f2 = norm2(f);
+                if (f2 >= T(Tol<T>::stall) * f2prev) break;
+                f2prev = f2;
             }
             const T dj = T(1) - norm2(K);
             if (!(fabs(dj) >= T(1e-30))) break;
