@@ -537,6 +537,9 @@ def run_fits(sblm, args, deadline, peaks):
 
     budget.run(out, "paper_workload", 90, lambda: run_paper_workload(sblm, w))
     budget.run(out, "paper_noisy_blended_workload", 90, lambda: run_noisy_blended_workload(sblm, w))
+    # the same noisy test at a longer budget (the paper's budget was 20 minutes per fit)
+    budget.run(out, "paper_noisy_blended_workload_long", 300,
+               lambda: run_noisy_blended_workload(sblm, w, n_gen=PAPER_GEN_LONG))
     return out
 
 
@@ -581,6 +584,7 @@ def run_seasonal(sblm):
 # the paper's own test shape (Section 4.2, noise-free): Table 1 ranges, 100 evenly spaced epochs over
 # t0 +- (2..3) tE, sigma 0.01 mag; success per number of peaks, EA + amoeba as in Table 2
 PAPER_LCS, PAPER_POP, PAPER_GEN = 256, 1000, 3000
+PAPER_GEN_LONG = 10000
 PAPER_TABLE2_EA_AMOEBA = {"1": [97, 100], "2": [98, 100], "3": [97, 98], "4": [94, 94]}  # strict, weak (%)
 # the paper's noisy, blended test (Section 4.4): as above with epochs drawn at random, the noise
 # model of Section 2.4 (m0 in Table 1's [18, 22]) and a blending fraction f in (0, 1], fitted
@@ -605,7 +609,7 @@ def _peak_classes(sblm, b, n_lc):
     return np.concatenate(A), np.array(peaks)
 
 
-def _paper_arms(sblm, w, b, dev, lo, hi, precision, chi_true, nu, peaks, f_true=None, m0=None):
+def _paper_arms(sblm, w, b, dev, lo, hi, precision, chi_true, nu, peaks, f_true=None, m0=None, n_gen=None):
     """EA + amoeba on the paper-shaped curves, plain and proposal-seeded. Success as in Section 4.2:
     strict = some returned model (every evaluated population, through the device's success
     monitor, or the polished best) has delta chi^2 / nu < 1 and every parameter within 10%; weak =
@@ -615,7 +619,7 @@ def _paper_arms(sblm, w, b, dev, lo, hi, precision, chi_true, nu, peaks, f_true=
     sl = [slice(b.offsets[i], b.offsets[i + 1]) for i in range(len(chi_true))]
     out = {}
     for label, frac in (("plain_mixed", 0.0), ("seeded_mixed", SEED_FRAC)):
-        p = sblm.params(n_pop=PAPER_POP, n_gen=PAPER_GEN, precision=precision, seed=1, polish_fev=FIT_POLISH)
+        p = sblm.params(n_pop=PAPER_POP, n_gen=n_gen or PAPER_GEN, precision=precision, seed=1, polish_fev=FIT_POLISH)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         best, chi, first = sblm.fit_batch_monitored(*dev, lo, hi, p, b.truth, chi_true + nu, f_ref=f_true,
@@ -686,7 +690,7 @@ def run_paper_workload(sblm, w):
     return out
 
 
-def run_noisy_blended_workload(sblm, w):
+def run_noisy_blended_workload(sblm, w, n_gen=None):
     import torch
 
     from paper_1208_4830_gb300 import synth
@@ -701,12 +705,12 @@ def run_noisy_blended_workload(sblm, w):
     out = {"workload": f"{PAPER_LCS} noisy, blended curves of the paper's second test (Table 1 ranges, 100 random "
                        f"epochs, noise model of Section 2.4 at the true magnitude, m0 the source's unlensed magnitude in "
                        f"[18, 22], f in (0, 1]); blended chi^2 with f profiled out; "
-                       f"N_pop {PAPER_POP} x {PAPER_GEN} generations + amoeba ({FIT_POLISH} evaluations)",
+                       f"N_pop {PAPER_POP} x {n_gen or PAPER_GEN} generations + amoeba ({FIT_POLISH} evaluations)",
            "curves_per_peak_class": {str(k): int(np.sum(peaks == k)) for k in (1, 2, 3, 4)},
            "paper_table3_ea_amoeba_strict_weak_pct": PAPER_TABLE3_EA_AMOEBA}
     # nu = 100 - 7: six lens and trajectory parameters plus f
     out.update(_paper_arms(sblm, w, b, dev, synth.PAPER_LO, synth.PAPER_HI, "mixed+blend", chi_true, 100 - 7, peaks,
-                           f_true=b.f, m0=b.m0))
+                           f_true=b.f, m0=b.m0, n_gen=n_gen))
     return out
 
 
