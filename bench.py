@@ -55,6 +55,10 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # scaled by the magnifications (the dense term rows, 8 B per magnification, dominate)
 FLOP_COUNT = {"mixed": {"fp32_per_mag": 2387.8, "fp64_per_mag": 10.51, "traffic": 2.77e9,
                         "file": "profiles/forward_kernel_mixed_sweep_32x4096x2000.md"}}
+# the FP64 mode on one population of 4096 (256 threads per candidate, runs of 8 epochs): FP64
+# operations per magnification, counted the same way
+# (python tests/host_solver/count_workload.py --fp64 --pops 1 --stride 16 --seg 8)
+FP64_CONTEXT_FLOP_PER_MAG = 3416.4
 
 
 def set_populations(n):
@@ -231,8 +235,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
         m = e0.elapsed_time(e1) / n
         by_prec[prec] = {"ms_per_step": m, "value": n_p * N_CAND * N_EP / m * 1e3, "populations": n_p}
+        if prec == "fp64":  # the FP64 forward model against the FP64 pipe's measured rate
+            by_prec[prec]["fp64_flop_per_magnification"] = FP64_CONTEXT_FLOP_PER_MAG
+            by_prec[prec]["achieved_fp64_tflops"] = FP64_CONTEXT_FLOP_PER_MAG * n_p * N_CAND * N_EP / (m * 1e-3) / 1e12
 
     peaks = measured_peaks(sblm, local, clk) if rank == 0 else None
+    if peaks and "fp64" in by_prec:
+        by_prec["fp64"]["frac_of_measured_fp64_rate"] = by_prec["fp64"]["achieved_fp64_tflops"] / peaks["fp64_measured"]
     fits = None
     if args.extras and args.fits and world == 1:  # the fit workloads run on one GPU only
         fits = run_fits(sblm, args, deadline=t_start + args.time_budget, peaks=peaks)

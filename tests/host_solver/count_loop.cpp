@@ -5,6 +5,7 @@
 //
 // Binary input: int32 n_rows, n_ep, seg; double t[n_ep]; double F[n_ep]; double w[n_ep] (1/sigma);
 // double theta[n_rows][6]. Runs of `seg` epochs start cold, as one device thread's segment does.
+// With "--fp64" the FP64 mode's loop is counted instead (every epoch solved in FP64).
 // Text output: epochs, FP32 operations, FP64 operations, epochs re-solved in FP64.
 #include <cstdio>
 #include <cstring>
@@ -40,8 +41,10 @@ static int pins() {
 
 int main(int argc, char** argv) {
     if (argc == 2 && std::strcmp(argv[1], "--pins") == 0) return pins();
-    if (argc != 2) return 2;
-    FILE* fi = fopen(argv[1], "rb");
+    // "--fp64 <input>": the FP64 mode's epoch loop instead of MIXED
+    const bool fp64 = argc == 3 && std::strcmp(argv[1], "--fp64") == 0;
+    if (argc != 2 && !fp64) return 2;
+    FILE* fi = fopen(argv[argc - 1], "rb");
     if (!fi) return 2;
     int hdr[3];
     if (fread(hdr, sizeof(int), 3, fi) != 3) return 1;
@@ -52,7 +55,23 @@ int main(int argc, char** argv) {
     if (fread(w.data(), 8, n_ep, fi) != (size_t)n_ep) return 1;
     if (fread(th.data(), 8, th.size(), fi) != th.size()) return 1;
     unsigned long long deferred = 0;
-    for (int r = 0; r < n_rows; ++r) {
+    for (int r = 0; fp64 && r < n_rows; ++r) {
+        const double* p = &th[6 * (size_t)r];
+        const double t0 = p[0], inv_tE = 1.0 / p[1], u0 = p[2], d = p[4], q = p[5];
+        double sa, ca;
+        sincos(p[3], &sa, &ca);
+        cx<CD> z[5];
+        bool warm = false;
+        for (int e = 0; e < n_ep; ++e) {
+            if (e % seg == 0) warm = false;
+            const CD tau = (CD(t[e]) - CD(t0)) * CD(inv_tE);
+            const cx<CD> zeta = mk<CD>(tau * CD(sa) + CD(u0) * CD(ca), -tau * CD(ca) + CD(u0) * CD(sa));
+            const EpochOut<CD> o = solve_epoch<CD>(zeta, CD(d), CD(q), z, warm);
+            const CD rr = (CD(F[e]) - o.A) * CD(w[e]);
+            (void)(rr * rr + CD(0.0));
+        }
+    }
+    for (int r = 0; !fp64 && r < n_rows; ++r) {
         // the candidate's decode (once per thread group on the device) is not counted per epoch
         const double* p = &th[6 * (size_t)r];
         const double t0 = p[0], inv_tE = 1.0 / p[1], u0 = p[2], d = p[4], q = p[5];

@@ -8,6 +8,9 @@ thread (the launch shape the library picks for that size). This script counts ev
 mean operations per magnification:
 
     python tests/host_solver/count_workload.py [--stride 16] [--seg 250]
+
+With --fp64 --pops 1 --seg 8 it counts the FP64 mode on one population of 4096 candidates (the
+launch shape of the benchmark's FP64 context line: 256 threads per candidate, runs of 8 epochs).
 """
 from __future__ import annotations
 
@@ -32,6 +35,7 @@ def main():
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--seg", type=int, default=250)
     ap.add_argument("--pops", type=int, default=32)
+    ap.add_argument("--fp64", action="store_true", help="count the FP64 mode (every epoch in FP64)")
     a = ap.parse_args()
     sw = synth.forward_sweep(4096, 2000, seed=0)
     thetas = [sw.theta] + [synth.forward_sweep(4096, 16, seed=1000 * k).theta for k in range(1, a.pops)]
@@ -42,7 +46,7 @@ def main():
     wd = tempfile.mkdtemp(prefix="sblm_count_")
     host_build.build(wd)
     exe = host_build.build_count(wd)
-    n, f32, f64, deferred = host_build.count(exe, theta, sw.t, flux, sigma, a.seg, wd)
+    n, f32, f64, deferred = host_build.count(exe, theta, sw.t, flux, sigma, a.seg, wd, fp64=a.fp64)
     print(f"rows {theta.shape[0]} epochs {n} runs of {a.seg}: fp32/mag {f32 / n:.1f} fp64/mag {f64 / n:.2f} "
           f"re-solved {deferred / n:.5f} fp64/re-solved epoch {f64 / max(1, deferred):.0f}")
 

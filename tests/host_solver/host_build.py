@@ -79,9 +79,10 @@ def aberth_order(workdir: str):
     return tuple(int(x) for x in out)
 
 
-def count(exe: str, theta, t, flux, sigma, seg: int, workdir: str):
+def count(exe: str, theta, t, flux, sigma, seg: int, workdir: str, fp64: bool = False):
     """(epochs, FP32 operations, FP64 operations, epochs re-solved in FP64) of the MIXED epoch
-    loop over every (row, epoch); runs of ``seg`` epochs start cold."""
+    loop (or, with ``fp64``, the FP64 mode's loop) over every (row, epoch); runs of ``seg`` epochs
+    start cold."""
     theta = np.ascontiguousarray(theta, dtype=np.float64)
     n, m = theta.shape[0], np.asarray(t).size
     src = os.path.join(workdir, "count_in.bin")
@@ -90,7 +91,8 @@ def count(exe: str, theta, t, flux, sigma, seg: int, workdir: str):
         for a in (t, flux, 1.0 / np.asarray(sigma, dtype=np.float64)):
             np.ascontiguousarray(a, dtype=np.float64).tofile(f)
         theta.tofile(f)
-    out = subprocess.run([exe, src], check=True, capture_output=True, text=True).stdout.split()
+    args = [exe, "--fp64", src] if fp64 else [exe, src]
+    out = subprocess.run(args, check=True, capture_output=True, text=True).stdout.split()
     return tuple(int(x) for x in out)
 
 
