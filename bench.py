@@ -339,7 +339,7 @@ HEAD_LCS, BIG_LCS, FIT_EP, FIT_POP, FIT_GEN, FIT_POLISH = 152, 2000, 500, 1024, 
 FIT_STARTS, FIT_RADIUS = 8, 0.05
 PROPOSAL_STEPS, PROPOSAL_BATCH = 1024, 1024  # 1,048,576 training curves
 SEED_FRAC = 0.5
-# mixed-precision error study: the first 1000 held-out curves (same recipe as BASELINE's)
+# mixed-precision error study: the first 1000 held-out curves (500 epochs at 2% noise)
 ERR_LCS = 1000
 # batched persistent fit of seasonal curves of uneven length (200-5000 epochs, 120-day gaps,
 # sigma 0.5-5%), N_pop 1024 x 300 generations, one graph-captured launch, autotuned launch shape
@@ -527,7 +527,7 @@ def run_fits(sblm, args, deadline, peaks):
 
     budget.run(out, "mixed_precision_error", 40, error_study)
     budget.run(out, "seasonal_batch", 260, lambda: run_seasonal(sblm))
-    # all 2000 held-out curves (BASELINE's learned-proposal test): seeded vs plain MIXED
+    # all 2000 held-out curves (the learned proposal's held-out test): seeded vs plain MIXED
     big = {"workload": f"{BIG_LCS} held-out curves, same recipe and budget"}
     out["heldout_2000"] = big
     res = {}
