@@ -333,7 +333,7 @@ def make_device_step(sblm, P_in, t, flux, sigma, precision, dev, n_pops):
 # fits/s comparison uses the same curves in every arm (the first HEAD_LCS, one per SM) and a
 # budget at which the arms reach 90% success at delta chi^2 <= 1; the MIXED arms also fit all
 # BIG_LCS held-out curves
-HEAD_LCS, BIG_LCS, FIT_EP, FIT_POP, FIT_GEN, FIT_POLISH = 152, 2000, 500, 1024, 900, 2000
+HEAD_LCS, BIG_LCS, FIT_EP, FIT_POP, FIT_GEN, FIT_POLISH = 152, 2000, 500, 1024, 1200, 2000
 # the amoeba runs from the 8 fittest distinct solutions of each fit (distinct: some gene differs by
 # more than 0.05) and keeps the best; the paper polishes the fittest only (polish_starts 1)
 FIT_STARTS, FIT_RADIUS = 8, 0.05
@@ -477,8 +477,8 @@ def run_fits(sblm, args, deadline, peaks):
                         f"batched persistent fitter"}
     out["head_to_head"] = head
     fits, head_best = {}, {}
-    for key, prec, frac, est in (("seeded_mixed", "mixed", SEED_FRAC, 45), ("plain_mixed", "mixed", 0.0, 45),
-                                 ("plain_fp64", "fp64", 0.0, 640)):
+    for key, prec, frac, est in (("seeded_mixed", "mixed", SEED_FRAC, 60), ("plain_mixed", "mixed", 0.0, 60),
+                                 ("plain_fp64", "fp64", 0.0, 860)):
         def go(prec=prec, frac=frac, key=key):
             r, best, _ = arm(prec, frac, HEAD_LCS)
             head_best[key] = best
@@ -526,7 +526,7 @@ def run_fits(sblm, args, deadline, peaks):
         return r
 
     budget.run(out, "mixed_precision_error", 40, error_study)
-    budget.run(out, "seasonal_batch", 260, lambda: run_seasonal(sblm))
+    budget.run(out, "seasonal_batch", 150, lambda: run_seasonal(sblm))
     # all 2000 held-out curves (the learned proposal's held-out test): seeded vs plain MIXED
     big = {"workload": f"{BIG_LCS} held-out curves, same recipe and budget"}
     out["heldout_2000"] = big
@@ -536,7 +536,7 @@ def run_fits(sblm, args, deadline, peaks):
             r, best, chi = arm("mixed", frac, BIG_LCS)
             res[key] = (best, chi)
             return r
-        budget.run(big, key, 480, go)
+        budget.run(big, key, 520, go)
     if len(res) == 2:
         ok_s = (res["seeded_mixed"][1] - chi_true) <= 1.0
         ok_p = (res["plain_mixed"][1] - chi_true) <= 1.0
@@ -896,7 +896,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fits", dest="fits", action="store_false", help="skip the fits/s measurement")
-    ap.add_argument("--time-budget", type=float, default=1080.0,
+    ap.add_argument("--time-budget", type=float, default=1320.0,
                     help="seconds from the start within which the optional fit workloads must finish; a workload "
                          "that would not fit is reported as skipped")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
