@@ -151,6 +151,14 @@ def build_inputs(seed=0):
     return sw, theta, P0
 
 
+def pipe_time_fraction(fp32_flop, fp64_flop, fp32_peak_tflops, fp64_peak_tflops, seconds):
+    """The time the FP32 and FP64 pipes would need for the given algorithmic work at their peak
+    rates, as a fraction of the measured time: the roofline fraction of a pass whose work is split
+    between the two pipes (an FP64 operation costs the FP32 pipe's rate / the FP64 pipe's rate as
+    much time as an FP32 one)."""
+    return (fp32_flop / (fp32_peak_tflops * 1e12) + fp64_flop / (fp64_peak_tflops * 1e12)) / seconds
+
+
 def measured_peaks(sblm, device_index, clk):
     """FP32 / FP64 peaks of this device: nominal (SMs x lanes x 2 flop x maximum SM clock) and
     measured (sblm_peak_rates: FMA chains on every SM)."""
@@ -267,6 +275,10 @@ def run_gpu(args):
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None,
                          "frac_of_measured_fma_rate": (achieved / peaks["fp32_measured"]) if achieved else None,
+                         "frac_pipe_time": pipe_time_fraction(f32 * mags, fc.get("fp64_per_mag", 0.0) * mags, peak,
+                                                              peaks["fp64_measured"], fwd * 1e-3) if f32 else None,
+                         "frac_pipe_time_note": "(FP32 work / FP32 peak + FP64 re-solve work / measured FP64 rate) "
+                                                "/ forward-pass time",
                          "traffic": fc.get("traffic"), "kernel_ms": fwd,
                          "fp32_flop_per_magnification": f32, "fp64_flop_per_magnification": fc.get("fp64_per_mag"),
                          "flop_count": "algorithmic: every FP32 operation of the solver as written, counted by the "

@@ -26,3 +26,11 @@ def test_success_criteria_by_hand():
 def test_whole_job_rate():
     # units processed by all ranks over the slowest rank's time per step
     assert bench.whole_job_rate(4, 1000, 2.0) == 4 * 1000 / 2.0 * 1e3
+
+
+def test_pipe_time_fraction():
+    # 80 TFLOP of FP32 at 80 TFLOP/s is 1 s, 1.25 TFLOP of FP64 at 1.25 TFLOP/s another 1 s: at
+    # those peaks the pass would take 2 s; measured 8 s gives 0.25
+    assert bench.pipe_time_fraction(80e12, 1.25e12, 80.0, 1.25, 8.0) == 0.25
+    # no FP64 work: the plain FP32 fraction
+    assert bench.pipe_time_fraction(40e12, 0.0, 80.0, 1.25, 1.0) == 0.5
