@@ -52,8 +52,8 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # (python tests/host_solver/count_workload.py --stride 16 --seg 250: 8192 of the 131072 candidates, every
 # epoch; 0.341% of the epochs re-solved in FP64, 3087 FP64 operations each). traffic: DRAM bytes
 # read + written per forward_kernel launch of the full step, from an ncu capture of 20 populations
-# scaled by the magnifications (the dense term rows, 8 B per magnification, dominate)
-FLOP_COUNT = {"mixed": {"fp32_per_mag": 2387.8, "fp64_per_mag": 10.51, "traffic": 2.77e9,
+# scaled by the magnifications (the dense term rows, 8 B per magnification, and register spills)
+FLOP_COUNT = {"mixed": {"fp32_per_mag": 2387.8, "fp64_per_mag": 10.51, "traffic": 3.58e9,
                         "file": "profiles/forward_kernel_mixed_sweep_32x4096x2000.md"}}
 # the FP64 mode on one population of 4096 (256 threads per candidate, runs of 8 epochs): FP64
 # operations per magnification, counted the same way
