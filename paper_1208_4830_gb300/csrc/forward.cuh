@@ -247,9 +247,9 @@ constexpr float kSpuriousPair = 0.25f;
 // Spurious-root rejection (Section 2.2: substitution into Eq. (lensing)) and magnification.
 // Each root gets up to `polish` Newton steps on the lens equation itself,
 //   delta = (-f + K conj(f)) / (1 - |K|^2),
-// (fewer once a step is below the rounding level or the residual stalls, Tol::stall) and keeps its
-// unpolished value if that moved it by more than half its distance to the
-// nearest other root. Images: relative residual |f| / (|z| + 1/|z| + q/|d - z| + |zeta|) at
+// fewer once a step is below the rounding level or the residual stalls (Tol::stall), and keeps
+// its unpolished value if that moved it by more than half its distance to the nearest other
+// root. Images: relative residual |f| / (|z| + 1/|z| + q/|d - z| + |zeta|) at
 // most Tol::lens; the count must be 3 or 5, the parities (sign of det J) must sum to -1 and no
 // two images may coincide; otherwise the 3 smallest residuals are taken, plus the 4th and 5th
 // when both are at most Tol::pair, and the epoch is flagged.
