@@ -34,3 +34,19 @@ def test_pipe_time_fraction():
     assert bench.pipe_time_fraction(80e12, 1.25e12, 80.0, 1.25, 8.0) == 0.25
     # no FP64 work: the plain FP32 fraction
     assert bench.pipe_time_fraction(40e12, 0.0, 80.0, 1.25, 1.0) == 0.5
+
+
+def test_budget_runs_what_fits_and_reports_the_rest():
+    import time
+
+    out = {}
+    b = bench.Budget(time.perf_counter() + 10.0)
+    assert b.run(out, "small", 1.0, lambda: {"ok": 1}) == {"ok": 1}
+    assert b.run(out, "large", 100.0, lambda: {"ok": 2}) is None
+    assert out["small"] == {"ok": 1} and out["large"]["skipped"].startswith("time budget")
+
+    def fails():
+        raise ValueError("boom")
+
+    b.run(out, "broken", 1.0, fails)  # a failing section is reported, not raised
+    assert out["broken"] == {"error": "ValueError: boom"}
