@@ -5,8 +5,6 @@ Given the same population, fitness and Philox key, the device must draw the same
 take the same integer decisions (ranks, parents, modes, jumps, restarts); genes then agree bit
 for bit except where exp() enters the creep step, where they may differ by an ulp or two.
 """
-import ctypes
-
 import numpy as np
 import pytest
 import torch

@@ -7,7 +7,6 @@ import pytest
 from scipy import stats
 
 from oracle import ea
-from oracle import philox as ph
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
